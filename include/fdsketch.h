@@ -1,0 +1,158 @@
+/*
+ * fdsketch.h -- C ABI of the GB300 buffered Frequent Directions library.
+ *
+ * Method: Desai, Ghashami, Phillips, "Improved Practical Matrix Sketching with
+ * Guarantees". A stream of rows a_i in R^d (Sec. 1.1, notation) is summarised
+ * by an ell x d sketch B whose covariance B^T B approximates A^T A; the error
+ * is cov-err = ||A^T A - B^T B||_2 / ||A||_F^2 (Sec. 1.1, "Error measures").
+ * The update is Algorithm 1 (Sec. 2.3) with one of four ReduceRank rules:
+ * FD (Sec. 2.3), parameterised FD (Algorithm 2, Sec. 3.1), SpaceSaving
+ * Directions (Algorithm 3, Sec. 3.1) and iterative SVD (Sec. 2.3).
+ *
+ * Buffered form. The device keeps a 2*ell-row working buffer. When it is
+ * full, one reduction runs entirely on the GPU: Gram G = B B^T, symmetric
+ * eigensolve G = U diag(sigma^2) U^T, the variant's sigma' (FP64), and the
+ * rotate B' = diag(sigma'/sigma) U^T B, which leaves ell-1 rows. The
+ * index rules use ell itself (delta = sigma_ell^2 of the 2*ell rows: Fast FD,
+ * Sec. 2.3). A reduction therefore fires after the first 2*ell rows and then
+ * every ell+1 rows, independent of the data.
+ *
+ * Conventions for every call:
+ *  - Return 0 on success or a negative FD_E* code; fd_strerror() names it.
+ *    No C++ exception crosses this boundary.
+ *  - Row data is row-major; `ld` is the distance in elements between rows
+ *    (ld >= d). `dtype` is FD_F32, FD_BF16 (raw bfloat16 bits) or FD_F64.
+ *  - `on_device` != 0: the pointer is CUDA device memory. The call is ordered
+ *    on the handle's stream; the caller keeps the memory valid until that
+ *    stream has passed the call (as with cudaMemcpyAsync).
+ *    `on_device` == 0: host memory; the call copies it through pinned staging
+ *    before it returns, so the caller may reuse it at once.
+ *  - The library owns all device state of a handle; the caller owns every
+ *    pointer it passes in.
+ *  - Calls on one handle must not overlap from several host threads.
+ */
+#ifndef FDSKETCH_H_
+#define FDSKETCH_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ReduceRank variants. FD: sigma'_j = sqrt(max(sigma_j^2 - delta, 0)),
+ * delta = sigma_ell^2 (Sec. 2.3). PFD: the first floor((1-alpha)*ell) values
+ * are kept, the rest up to ell shrink by delta = sigma_ell^2, values past ell
+ * are zeroed (Algorithm 2). SS: the second-smallest direction's squared value
+ * is added to the smallest and the second-smallest is freed, repeated until
+ * ell-1 directions remain; empty directions are freed first (Algorithm 3).
+ * ISVD: sigma'_j = sigma_j for j < ell, else 0 (Sec. 2.3). */
+enum { FD_VAR_FD = 0, FD_VAR_PFD = 1, FD_VAR_SS = 2, FD_VAR_ISVD = 3 };
+
+/* Arithmetic of the reduction.
+ * FD_PREC_FP32:   FP32 buffer, FP32 CUDA-core Gram and rotate, FP32 Jacobi
+ *                 eigensolve; shrink and bookkeeping in FP64.
+ * FD_PREC_BF16X3: buffer held as bfloat16 hi/lo pairs; Gram and rotate on the
+ *                 tcgen05 tensor cores as split products hi*hi + hi*lo + lo*hi
+ *                 accumulated in FP32 (TMEM); FP32 Jacobi; FP64 shrink.
+ * FD_PREC_FP64:   FP64 buffer, FP64 Gram, rotate and Jacobi (slow; for
+ *                 checking against FP64 references). */
+enum { FD_PREC_FP32 = 0, FD_PREC_BF16X3 = 1, FD_PREC_FP64 = 2 };
+
+enum { FD_F32 = 0, FD_BF16 = 1, FD_F64 = 2 };
+
+enum {
+  FD_OK = 0,
+  FD_EINVAL = -1,  /* bad argument: null pointer, d < 1, ell < 2,
+                      2*ell > FD_MAX_BUFFER_ROWS, alpha outside (0,1] for PFD,
+                      ld < d, unknown enum, precision not built */
+  FD_ENOMEM = -2,  /* a device or pinned host allocation failed */
+  FD_ECUDA = -3,   /* a CUDA call failed; fd_strerror(FD_ECUDA) gives the text
+                      of the last one */
+  FD_ENOCONV = -4, /* an eigensolve reached its sweep cap; the result is still
+                      written and the count is in fd_stats_t.noconv */
+  FD_EBUSY = -5    /* serving: no room to admit the request now */
+};
+
+#define FD_MAX_BUFFER_ROWS 512 /* 2*ell limit of one sketch */
+
+typedef struct fd_state* fd_handle;
+
+typedef struct {
+  int64_t d;
+  int32_t ell;
+  int32_t variant;
+  double alpha;
+  int32_t prec;
+  int32_t pending;        /* rows held in the buffer (ell-1 .. 2*ell-1) */
+  int64_t n_seen;         /* rows appended so far */
+  int64_t reductions;     /* reductions run by fd_append */
+  int64_t noconv;         /* eigensolves that hit the sweep cap */
+  double norm_a2;         /* ||A||_F^2 of the rows seen, FP64 */
+  double sum_delta;       /* Delta = sum of every delta subtracted (Sec. 3.1) */
+  double last_delta;      /* delta of the latest reduction */
+  double removed;         /* sum over reductions of sum_j (sigma_j^2 - sigma'_j^2) */
+  double max_sweeps;      /* largest Jacobi sweep count seen */
+  /* Totals including the final flush reduction of the latest fd_sketch call
+   * (equal to the fields above when it had nothing to flush): */
+  double sketch_sum_delta;
+  double sketch_removed;
+  double sketch_norm_b2;  /* ||B||_F^2 of the sketch fd_sketch returned */
+} fd_stats_t;
+
+/* Create a sketch of width d with ell output rows (fd_sketch returns ell x d;
+ * the last row is always zero, as in Algorithm 1 a reduced sketch uses at most
+ * ell-1 rows). alpha is used by FD_VAR_PFD only. cuda_stream is a
+ * cudaStream_t (NULL = the legacy default stream). Allocates all device state. */
+int fd_create(int64_t d, int32_t ell, int32_t variant, double alpha, int32_t prec,
+              void* cuda_stream, fd_handle* out);
+
+/* Append n rows (Algorithm 1's loop body, "insert a_i", reducing whenever the
+ * 2*ell buffer is full). n = 0 is a no-op. Asynchronous for device rows. */
+int fd_append(fd_handle h, const void* rows, int64_t n, int64_t ld, int32_t dtype,
+              int32_t on_device);
+
+/* Write the sketch B (ell x d, row-major, leading dimension d) to out in
+ * `dtype` (FD_F32 or FD_F64). Non-destructive: if more than ell-1 rows are
+ * pending, one more reduction with the same index rules runs on a copy (the
+ * returned B then includes it; the handle's state is unchanged). For host
+ * output the call synchronises the stream. */
+int fd_sketch(fd_handle h, void* out, int32_t dtype, int32_t out_on_device);
+
+/* cov-err(A, B) = ||A^T A - B^T B||_2 / ||A||_F^2 (Sec. 1.1) for the handle's
+ * current sketch B (as fd_sketch returns it) and the n x d matrix A, with
+ * ||.||_2 = max |eigenvalue| (Sec. 1.1, the maximum of |(||Ax||^2 - ||Bx||^2)|
+ * over unit x). Lanczos with full reorthogonalisation on the GPU; every
+ * matrix-vector product streams A once and never forms the d x d matrix.
+ * Synchronises the stream; *cov_err receives the value. */
+int fd_cov_err(fd_handle h, const void* A, int64_t n, int64_t ld, int32_t dtype,
+               int32_t on_device, double* cov_err);
+
+/* Same evaluator for a caller-given sketch B (rows x d, row-major FP32/FP64
+ * per dtype, leading dimension d), without a handle. stream may be NULL. */
+int fd_cov_err_pair(const void* A, int64_t n, int64_t d, int64_t lda, int32_t a_dtype,
+                    const void* B, int64_t rows, int32_t b_dtype, int32_t on_device,
+                    void* cuda_stream, double* cov_err, double* lambda_min,
+                    double* lambda_max);
+
+/* Counters of the handle (synchronises the stream). */
+int fd_stats(fd_handle h, fd_stats_t* s);
+
+/* Spectrum of the latest reduction run by fd_append: sigma^2 (descending,
+ * 2*ell values) and sigma'^2 aligned with it, FP64, host arrays of 2*ell. */
+int fd_last_spectrum(fd_handle h, double* sigma2, double* sigma_prime2);
+
+/* Release every resource of the handle (synchronises its stream). */
+int fd_destroy(fd_handle h);
+
+/* Text for an FD_E* code (static storage). */
+const char* fd_strerror(int32_t code);
+
+/* Library version and the sm architecture it was built for. */
+const char* fd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDSKETCH_H_ */

@@ -61,7 +61,7 @@ def shrink_index_split(ell: int, alpha: float) -> int:
     A tiny epsilon guards ``(1-alpha)*ell`` computed as e.g. 39.99999.
     """
     keep = int(math.floor((1.0 - alpha) * ell + 1e-9))
-    keep = max(0, min(ell, keep))
+    keep = max(0, min(ell - 1, keep))   # alpha > 0: at least one value shrinks
     return ell - keep
 
 

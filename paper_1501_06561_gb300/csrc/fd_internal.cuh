@@ -1,0 +1,92 @@
+// Internal declarations shared by the translation units of libfdsketch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "fdsketch.h"
+
+namespace fdk {
+
+// FP64 bookkeeping of one sketch, kept on the device so that a whole
+// reduction (Gram -> eigensolve -> shrink -> rotate) needs no host round trip.
+struct DevCounters {
+  double norm_a2;      // ||A||_F^2 of the rows ingested so far
+  double sum_delta;    // Delta (Sec. 3.1): every delta subtracted
+  double last_delta;
+  double removed;      // sum_j (sigma_j^2 - sigma'_j^2) over reductions
+  double norm_b2;      // ||B||_F^2 after the latest reduction
+  double max_sweeps;
+  long long reductions;
+  long long noconv;
+  unsigned int ingest_ticket;  // last-block-done counter of the ingest kernel
+  int retained;                // rows with sigma' > 0 after the latest reduction
+};
+
+// Parameters of the fused eigensolve + shrink kernel (one CTA per reduction).
+struct EigArgs {
+  const void* parts;   // Gram partial sums: nparts slices of ldp x ldp (T)
+  int nparts;
+  int ldp;
+  long long part_stride;  // elements between slices
+  int symmetrize;      // 1: G = (Z + Z^T) / 2 (split-precision products)
+  int n;               // rows being reduced (2*ell, or fewer at a flush)
+  int ell;
+  int variant;
+  double alpha;
+  void* work;          // global G when it does not fit in shared memory (n x ldw)
+  int ldw_work;
+  const DevCounters* ctr_in;
+  DevCounters* ctr_out;
+  double* sig2_out;    // sorted sigma^2 (n) or null
+  double* sigp2_out;   // sigma'^2 aligned with it, or null
+  void* wrot;          // rotate matrix rows 0..ell-2 (T), ld = ldr
+  int ldr;
+  __nv_bfloat16* wrot_hi;  // optional split copies (BF16 hi / lo) for tcgen05
+  __nv_bfloat16* wrot_lo;
+  int ldr16;
+  int max_sweeps;
+  double tol;          // rotate when |gamma| > tol * sqrt(alpha * beta)
+};
+
+// --- launchers (fd_simt.cu) -------------------------------------------------
+cudaError_t launch_ingest(const void* src, int64_t n, int64_t ld, int dtype,
+                          void* dst, int64_t ldd, int dst_is_f64, int64_t d,
+                          double* rownorm_scratch, DevCounters* ctr,
+                          __nv_bfloat16* rm_hi, __nv_bfloat16* rm_lo2, int64_t ld_rm,
+                          __nv_bfloat16* cm_hi, __nv_bfloat16* cm_lo, int64_t ld_cm,
+                          int row0, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_gram_simt(const T* B, int64_t ldb, int n, int64_t d, T* parts,
+                             int ldp, int ksplit, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_eig_shrink(const EigArgs& a, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_rotate_simt(const T* W, int ldw, int nout, int n, const T* Bin,
+                               int64_t ldb, T* Bout, int64_t ldo, int64_t d,
+                               cudaStream_t st);
+
+cudaError_t launch_convert_out(const void* src, int src_f64, int64_t lds, int rows,
+                               int64_t d, void* dst, int dst_f64, int64_t ldd,
+                               int zero_from_row, cudaStream_t st);
+
+cudaError_t launch_norm_b2(const void* src, int src_f64, int64_t lds, int rows,
+                           int64_t d, DevCounters* ctr, cudaStream_t st);
+
+// --- tensor-core path (fd_tc.cu) ---------------------------------------------
+struct TcPlanes;  // opaque, defined in fd_tc.cu
+int tc_available();
+
+// --- cov-err evaluator (fd_coverr.cu) ---------------------------------------
+int cov_err_device(const void* A, int64_t n, int64_t d, int64_t lda, int a_f64,
+                   const void* B, int64_t rows, int64_t ldb, int b_f64,
+                   cudaStream_t st, double* cov, double* lmin, double* lmax);
+
+// Records the text of the last failing CUDA call (for fd_strerror).
+void set_cuda_error(cudaError_t e, const char* where);
+
+}  // namespace fdk

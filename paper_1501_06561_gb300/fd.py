@@ -1,0 +1,211 @@
+"""ctypes binding of libfdsketch (C ABI in include/fdsketch.h).
+
+Argument marshalling only: every step of the sketch update runs in the CUDA
+kernels of the library. Tensors on a CUDA device are passed as device
+pointers on PyTorch's current stream; numpy arrays and CPU tensors are passed
+as host pointers (the library stages them through pinned memory). The library
+is loaded on first use; if it has not been built, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfdsketch.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "fdsketch.h")
+
+VARIANT = {"fd": 0, "pfd": 1, "ss": 2, "isvd": 3}
+PREC = {"fp32": 0, "bf16x3": 1, "fp64": 2}
+F32, BF16, F64 = 0, 1, 2
+ERR = {0: "FD_OK", -1: "FD_EINVAL", -2: "FD_ENOMEM", -3: "FD_ECUDA", -4: "FD_ENOCONV",
+       -5: "FD_EBUSY"}
+
+_lib = None
+
+
+class FDError(RuntimeError):
+    def __init__(self, code: int, where: str, text: str):
+        super().__init__(f"{where}: {ERR.get(code, code)} ({text})")
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int64), ("ell", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("alpha", ctypes.c_double), ("prec", ctypes.c_int32), ("pending", ctypes.c_int32),
+                ("n_seen", ctypes.c_int64), ("reductions", ctypes.c_int64),
+                ("noconv", ctypes.c_int64), ("norm_a2", ctypes.c_double),
+                ("sum_delta", ctypes.c_double), ("last_delta", ctypes.c_double),
+                ("removed", ctypes.c_double), ("max_sweeps", ctypes.c_double),
+                ("sketch_sum_delta", ctypes.c_double), ("sketch_removed", ctypes.c_double),
+                ("sketch_norm_b2", ctypes.c_double)]
+
+
+def load():
+    """Load libfdsketch.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run "
+                           "`python -m paper_1501_06561_gb300.build` (nvcc, sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "fd_create": [i64, i32, i32, dbl, i32, vp, ctypes.POINTER(vp)],
+        "fd_append": [vp, vp, i64, i64, i32, i32],
+        "fd_sketch": [vp, vp, i32, i32],
+        "fd_cov_err": [vp, vp, i64, i64, i32, i32, ctypes.POINTER(dbl)],
+        "fd_cov_err_pair": [vp, i64, i64, i64, i32, vp, i64, i32, i32, vp,
+                            ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
+        "fd_stats": [vp, ctypes.POINTER(Stats)],
+        "fd_last_spectrum": [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
+        "fd_destroy": [vp],
+        "fd_strerror": [i32],
+        "fd_version": [],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name in ("fd_strerror", "fd_version") else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions include/fdsketch.h declares."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fd_\w+)\s*\(", txt)))
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        lib = load()
+        raise FDError(code, where, lib.fd_strerror(code).decode())
+
+
+def _stream_ptr(stream):
+    if stream is not None:
+        return ctypes.c_void_p(stream)
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover
+        pass
+    return ctypes.c_void_p(0)
+
+
+def _as_rows(x):
+    """(pointer, n, ld, dtype code, on_device, keepalive) for a 2-D array/tensor."""
+    try:
+        import torch
+    except Exception:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(x, torch.Tensor):
+        if x.dim() == 1:
+            x = x.unsqueeze(0)
+        if x.stride(1) != 1:
+            x = x.contiguous()
+        code = {torch.float32: F32, torch.bfloat16: BF16, torch.float64: F64}.get(x.dtype)
+        if code is None:
+            raise TypeError(f"unsupported dtype {x.dtype}")
+        return (ctypes.c_void_p(x.data_ptr()), x.shape[0], x.stride(0), code,
+                1 if x.is_cuda else 0, x)
+    a = np.asarray(x)
+    if a.ndim == 1:
+        a = a[None, :]
+    if a.dtype not in (np.float32, np.float64) or a.strides[1] != a.itemsize:
+        a = np.ascontiguousarray(a, dtype=np.float64 if a.dtype == np.float64 else np.float32)
+    code = F32 if a.dtype == np.float32 else F64
+    return (ctypes.c_void_p(a.ctypes.data), a.shape[0], a.strides[0] // a.itemsize, code, 0, a)
+
+
+class FDSketch:
+    """One buffered FD sketch on the GPU (fd_create ... fd_destroy)."""
+
+    def __init__(self, d: int, ell: int, variant: str = "fd", alpha: float = 1.0,
+                 prec: str = "fp32", stream=None):
+        lib = load()
+        self.d, self.ell, self.variant, self.prec = d, ell, variant, prec
+        self._stream = _stream_ptr(stream)
+        h = ctypes.c_void_p()
+        _check(lib.fd_create(d, ell, VARIANT[variant], float(alpha), PREC[prec], self._stream,
+                             ctypes.byref(h)), "fd_create")
+        self._h = h
+
+    def append(self, rows):
+        ptr, n, ld, code, dev, keep = _as_rows(rows)
+        _check(load().fd_append(self._h, ptr, n, ld, code, dev), "fd_append")
+        return keep
+
+    def sketch(self, out=None, dtype=np.float64):
+        """B (ell x d). With ``out`` a CUDA tensor the result is written there."""
+        lib = load()
+        if out is not None:
+            import torch
+            code = F64 if out.dtype == torch.float64 else F32
+            _check(lib.fd_sketch(self._h, ctypes.c_void_p(out.data_ptr()), code, 1), "fd_sketch")
+            return out
+        B = np.empty((self.ell, self.d), dtype=dtype)
+        code = F64 if B.dtype == np.float64 else F32
+        _check(lib.fd_sketch(self._h, ctypes.c_void_p(B.ctypes.data), code, 0), "fd_sketch")
+        return B
+
+    def cov_err(self, A) -> float:
+        ptr, n, ld, code, dev, keep = _as_rows(A)
+        out = ctypes.c_double()
+        _check(load().fd_cov_err(self._h, ptr, n, ld, code, dev, ctypes.byref(out)), "fd_cov_err")
+        return out.value
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().fd_stats(self._h, ctypes.byref(s)), "fd_stats")
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def last_spectrum(self):
+        L = 2 * self.ell
+        a = np.zeros(L)
+        b = np.zeros(L)
+        _check(load().fd_last_spectrum(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "fd_last_spectrum")
+        return a, b
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fd_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cov_err_pair(A, B, stream=None):
+    """(cov-err, lambda_min, lambda_max) of A^T A - B^T B on the GPU."""
+    lib = load()
+    pa, n, lda, ca, da, ka = _as_rows(A)
+    pb, rows, ldb, cb, db, kb = _as_rows(B)
+    if da != db:
+        raise ValueError("A and B must both be on the device or both on the host")
+    d = (A.shape[1])
+    if ldb != d:
+        raise ValueError("B must be contiguous (leading dimension d)")
+    c, lo, hi = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib.fd_cov_err_pair(pa, n, d, lda, ca, pb, rows, cb, da, _stream_ptr(stream),
+                               ctypes.byref(c), ctypes.byref(lo), ctypes.byref(hi)),
+           "fd_cov_err_pair")
+    return c.value, lo.value, hi.value

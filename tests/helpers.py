@@ -1,0 +1,55 @@
+"""Shared assertions for the parity tests (GPU result vs FP64 oracle)."""
+import numpy as np
+
+# Tolerances: sketch singular values within 1e-4 relative and cov-err within
+# 1e-5 absolute of the FP64 oracle. "Relative" is read per value for every
+# sigma_j with sigma_j^2 >= 1e-6 ||A||_F^2; smaller values (shrunk to near
+# zero, where a relative bound is meaningless) are held to the same bound
+# taken at that threshold: |d sigma_j| <= 1e-4 * sqrt(1e-6 ||A||_F^2).
+SIG_REL = 1e-4
+SIG_FLOOR = 1e-6
+COV_ABS = 1e-5
+
+
+def sigmas(B):
+    return np.linalg.svd(np.asarray(B, dtype=np.float64), compute_uv=False)
+
+
+def small_value_floor(norm_a2, sigma1, buffer_rows=0, eps=0.0):
+    """sigma^2 below which a value counts as small: 1e-6 ||A||_F^2, raised to
+    the absolute resolution of the eigensolve's arithmetic (rows x eps x
+    sigma_1^2: a Gram eigensolve in precision eps resolves eigenvalues only
+    to about that, however it is done)."""
+    return max(SIG_FLOOR * norm_a2, buffer_rows * eps * sigma1 ** 2)
+
+
+def sigma_errors(s_gpu, s_orc, norm_a2, buffer_rows=0, eps=0.0):
+    k = min(len(s_gpu), len(s_orc))
+    s_gpu = np.asarray(s_gpu[:k], dtype=np.float64)
+    s_orc = np.asarray(s_orc[:k], dtype=np.float64)
+    thr = np.sqrt(small_value_floor(norm_a2, s_orc[0] if k else 0.0, buffer_rows, eps))
+    big = s_orc >= thr
+    d = np.abs(s_gpu - s_orc)
+    rel = np.where(big, d / np.maximum(s_orc, 1e-300), 0.0)
+    small_abs = np.where(~big, d, 0.0)
+    return float(rel.max(initial=0.0)), float(small_abs.max(initial=0.0) / thr)
+
+
+EPS32 = 2.0 ** -23
+# unit roundoff of the products each path forms (FP32; bfloat16 hi+lo pairs,
+# which carry about 16 significant bits; FP64)
+UNIT = {"fp32": 2.0 ** -24, "bf16x3": 2.0 ** -16, "fp64": 2.0 ** -53}
+
+
+def assert_sigma_parity(B_gpu, B_orc, norm_a2, prec, ell, what=""):
+    """P12 reading with the small-value floor raised to 2*ell*u*sigma_1^2, the
+    absolute eigenvalue resolution of a Gram eigensolve whose products carry
+    unit roundoff u (u per precision in UNIT)."""
+    return assert_sigma_close(B_gpu, B_orc, norm_a2, what=what, buffer_rows=2 * ell,
+                              eps=UNIT[prec])
+
+
+def assert_sigma_close(B_gpu, B_orc, norm_a2, rel=SIG_REL, what="", buffer_rows=0, eps=0.0):
+    r, s = sigma_errors(sigmas(B_gpu), sigmas(B_orc), norm_a2, buffer_rows, eps)
+    assert r <= rel and s <= rel, f"{what}: sigma rel err {r:.3e}, small-value err {s:.3e} (tol {rel})"
+    return r, s

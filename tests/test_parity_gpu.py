@@ -1,0 +1,177 @@
+"""GPU path vs the FP64 oracle on the same seeded inputs (through the C ABI).
+
+Sizes span several 64-wide tiles with ragged tails. Tolerances (tests/helpers):
+sketch singular values within 1e-4 relative (values below 1e-6 ||A||_F^2 held
+to the bound at that threshold), cov-err within 1e-5 absolute, FP64 counters
+(||A||_F^2, Delta) close to the oracle's.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import cov_err, fd_sketch, FDOracle
+from paper_1501_06561_gb300 import fd
+from paper_1501_06561_gb300 import workloads as W
+from helpers import COV_ABS, EPS32, assert_sigma_close, sigmas
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp32", "fp64"]
+
+
+def _alpha(v):
+    return 0.2 if v == "pfd" else 1.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    fd.load()
+
+
+def run_gpu(A, ell, variant, prec, alpha=None, chunks=None, device=True):
+    alpha = _alpha(variant) if alpha is None else alpha
+    with fd.FDSketch(A.shape[1], ell, variant, alpha, prec) as s:
+        X = torch.from_numpy(np.ascontiguousarray(A)).cuda() if device else A
+        if chunks is None:
+            s.append(X)
+        else:
+            for a, b in zip(chunks[:-1], chunks[1:]):
+                s.append(X[a:b])
+        B = s.sketch()
+        st = s.stats()
+    return B, st
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("variant", ["fd", "pfd", "isvd"])
+def test_parity_small_ragged(prec, variant):
+    """n = 3001 rows, d = 333 (5 tiles + ragged), ell = 23: ~130 reductions."""
+    A = W.random_noisy(3001, 333, m=12, seed=21, dtype=np.float32)
+    B, st = run_gpu(A, 23, variant, prec)
+    Bo, io = fd_sketch(A, 23, variant, _alpha(variant))
+    assert st["reductions"] == io["reductions"] - (1 if io["reductions"] > st["reductions"] else 0)
+    assert abs(st["norm_a2"] - io["normA2"]) <= 1e-12 * io["normA2"]
+    assert_sigma_close(B, Bo, io["normA2"], what=f"{variant}/{prec}")
+    ce_g, ce_o = cov_err(A, B), cov_err(A, Bo)
+    assert abs(ce_g - ce_o) <= COV_ABS, (ce_g, ce_o)
+    assert abs(st["sketch_sum_delta"] - io["sum_delta"]) <= 1e-4 * io["sum_delta"]
+    assert st["noconv"] == 0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_parity_ss_short_stream(prec):
+    """SS makes discrete merge choices; on short streams the oracle's own
+    sensitivity to input rounding is far below the tolerance."""
+    A = W.random_noisy(2 * 30 + 5 * 31 + 7, 257, m=10, seed=22, dtype=np.float32)
+    B, st = run_gpu(A, 30, "ss", prec)
+    Bo, io = fd_sketch(A, 30, "ss")
+    assert_sigma_close(B, Bo, io["normA2"], what=f"ss/{prec}")
+    assert abs(cov_err(A, B) - cov_err(A, Bo)) <= COV_ABS
+    # mass preserved (SS theorem): ||A||_F^2 = ||B||_F^2
+    assert abs(st["sketch_norm_b2"] - io["normA2"]) <= 1e-5 * io["normA2"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_parity_c0(prec):
+    """Random Noisy n=10000, d=500, ell=50, plain FD."""
+    A = W.random_noisy(10000, 500, m=30, seed=0, dtype=np.float64)
+    B, st = run_gpu(A, 50, "fd", prec)
+    Bo, io = fd_sketch(A, 50, "fd")
+    r, s = assert_sigma_close(B, Bo, io["normA2"], what=f"C0/{prec}")
+    ce_g, ce_o = cov_err(A, B), cov_err(A, Bo)
+    assert abs(ce_g - ce_o) <= COV_ABS
+    if prec == "fp64":
+        assert r < 1e-9 and abs(ce_g - ce_o) < 1e-10
+    assert abs(st["sketch_sum_delta"] - io["sum_delta"]) <= 1e-4 * io["sum_delta"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("variant", ["fd", "pfd", "ss", "isvd"])
+def test_single_reduction_spectrum(prec, variant):
+    """Exactly 2*ell rows: one reduction. The eigensolve's sigma^2 equals the
+    oracle's squared singular values of the buffer."""
+    ell = 37
+    A = W.random_noisy(2 * ell, 411, m=20, seed=23, dtype=np.float32)
+    with fd.FDSketch(411, ell, variant, _alpha(variant), prec) as s:
+        s.append(torch.from_numpy(A).cuda())
+        sig2, sigp2 = s.last_spectrum()
+        B = s.sketch()
+    _, io = fd_sketch(A, ell, variant, _alpha(variant), record=True)
+    so = io["records"][0]["sigma"] ** 2
+    spo = io["records"][0]["sigma_prime"] ** 2
+    tol = 2e-5 if prec == "fp32" else 1e-11
+    big = so >= 1e-6 * so[0]
+    np.testing.assert_allclose(sig2[big], so[big], rtol=tol)
+    np.testing.assert_allclose(sigp2, spo, rtol=0, atol=tol * so[0] * 4)
+    Bo, _ = fd_sketch(A, ell, variant, _alpha(variant))
+    assert_sigma_close(B, Bo, io["normA2"], what=f"1-red {variant}/{prec}")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_chunked_and_host_input_bit_identical(prec):
+    A = W.random_noisy(1000, 130, m=8, seed=24, dtype=np.float32)
+    B0, _ = run_gpu(A, 11, "fd", prec)
+    B1, _ = run_gpu(A, 11, "fd", prec, chunks=[0, 1, 5, 22, 23, 400, 999, 1000])
+    B2, _ = run_gpu(A, 11, "fd", prec, device=False)
+    np.testing.assert_array_equal(B0, B1)
+    np.testing.assert_array_equal(B0, B2)
+
+
+@pytest.mark.parametrize("variant", ["fd", "pfd", "ss", "isvd"])
+def test_exact_recovery_low_rank(variant):
+    ell = 9
+    A = W.low_rank_rows(700, 70, rank=ell - 1, dtype=np.float32)
+    B, st = run_gpu(A, ell, variant, "fp32")
+    assert cov_err(A, B) <= 1e-5
+
+
+def test_short_stream_returns_rows_and_edge_sizes():
+    A = W.random_noisy(6, 40, m=3, seed=25, dtype=np.float32)
+    B, st = run_gpu(A, 8, "fd", "fp32")
+    np.testing.assert_array_equal(B[:6], A.astype(np.float64))
+    assert np.all(B[6:] == 0) and st["reductions"] == 0
+    # smallest sketch: ell = 2, d = 1
+    A = W.random_noisy(50, 1, m=1, seed=26, dtype=np.float32)
+    B, st = run_gpu(A, 2, "fd", "fp32")
+    Bo, io = fd_sketch(A, 2, "fd")
+    assert abs(cov_err(A, B) - cov_err(A, Bo)) <= COV_ABS
+    # largest buffer: ell = 256 (512 rows)
+    A = W.random_noisy(1500, 300, m=40, seed=27, dtype=np.float32)
+    B, st = run_gpu(A, 256, "fd", "fp32")
+    Bo, io = fd_sketch(A, 256, "fd")
+    assert_sigma_close(B, Bo, io["normA2"], what="ell=256", buffer_rows=512, eps=EPS32)
+
+
+def test_input_dtypes_bf16_and_f64():
+    A = W.random_noisy(900, 200, m=10, seed=28, dtype="bf16")   # float32 holding bf16 values
+    with fd.FDSketch(200, 16, "fd", 1.0, "fp32") as s:
+        s.append(torch.from_numpy(A).cuda().to(torch.bfloat16))
+        B = s.sketch()
+    Bo, io = fd_sketch(A, 16, "fd")
+    assert_sigma_close(B, Bo, io["normA2"], what="bf16 input")
+    A64 = W.random_noisy(900, 200, m=10, seed=28, dtype=np.float64)
+    B, _ = run_gpu(A64, 16, "fd", "fp64")
+    Bo, io = fd_sketch(A64, 16, "fd")
+    assert_sigma_close(B, Bo, io["normA2"], rel=1e-9, what="f64 input")
+
+
+def test_cov_err_evaluator_matches_oracle():
+    rng = np.random.default_rng(5)
+    for (n, d, r) in [(5000, 300, 20), (20000, 1024, 64), (777, 65, 3)]:
+        A = W.random_noisy(n, d, m=min(10, d), seed=n, dtype=np.float32)
+        B = (rng.standard_normal((r, d)) * np.sqrt(n / d)).astype(np.float32)
+        c, lo, hi = fd.cov_err_pair(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda())
+        co = cov_err(A, B)
+        assert abs(c - co) <= 1e-7, (n, d, c, co)
+    # a real sketch (PSD difference) through the handle
+    A = W.random_noisy(4000, 500, m=30, seed=29, dtype=np.float32)
+    with fd.FDSketch(500, 40, "fd", 1.0, "fp32") as s:
+        At = torch.from_numpy(A).cuda()
+        s.append(At)
+        B = s.sketch()
+        c = s.cov_err(At)
+    assert abs(c - cov_err(A, B)) <= 1e-7
