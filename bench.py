@@ -1,0 +1,574 @@
+#!/usr/bin/env python3
+"""Throughput of the buffered Frequent Directions update on GB300.
+
+One step streams the whole synthetic matrix of the workload through the
+sketch (fd_reset, fd_append of every row, fd_sketch into device memory) and
+reports rows per second. Prints one JSON line (rank 0).
+
+Workloads (seeded synthetic inputs shaped like the paper's Random Noisy data,
+A = S D U + F / zeta, D from 1 to 0.1 over m signal dimensions):
+  c1  (default) n = 200,000, d = 2,000, m = 50, zeta = 10, FP32 rows, FD with
+      ell = 100, split-precision BF16x3 tensor-core path
+  c0  n = 10,000, d = 500, m = 30, ell = 50 (small case)
+Every option can be overridden (--ell, --variant, --prec, --n ...).
+
+--impl reference times the FP64 oracle (the plain CPU restatement of the
+method) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "c1": dict(n=200_000, d=2000, m=50, zeta=10.0, seed=1, ell=100, variant="fd", alpha=1.0,
+               prec="bf16x3", name="random-noisy n=200000 d=2000 k=50 zeta=10 fp32 rows"),
+    "c0": dict(n=10_000, d=500, m=30, zeta=10.0, seed=0, ell=50, variant="fd", alpha=1.0,
+               prec="fp32", name="random-noisy n=10000 d=500 m=30 zeta=10"),
+    "c3": dict(count=4096, seed=3, variant="fd", alpha=1.0, prec="fp32", ell=None, n=None,
+               name="batched: 4096 random-noisy streams, d in U{64..1024}, ell in U{16..64}, "
+                    "n in U{1000..50000}, k = ell/2, bf16 rows"),
+}
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS))
+    ap.add_argument("--ell", type=int)
+    ap.add_argument("--variant", choices=["fd", "pfd", "ss", "isvd"])
+    ap.add_argument("--alpha", type=float)
+    ap.add_argument("--prec", choices=["fp32", "bf16x3", "fp64"])
+    ap.add_argument("--n", type=int)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
+    ap.add_argument("--cpu-sample-rows", type=int, default=0)
+    ap.add_argument("--count", type=int, help="batched workload: number of sketches")
+    return ap.parse_args()
+
+
+def config(args):
+    w = dict(WORKLOADS[args.workload])
+    if args.workload == "c3":
+        for k in ("variant", "alpha"):
+            if getattr(args, k) is not None:
+                w[k] = getattr(args, k)
+        return w
+    for k in ("ell", "variant", "alpha", "prec", "n"):
+        v = getattr(args, k)
+        if v is not None:
+            w[k] = v
+    if w["variant"] == "pfd" and args.alpha is None:
+        w["alpha"] = 0.2
+    return w
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_rows(w, rank, rows=None):
+    from paper_1501_06561_gb300 import workloads
+    n = w["n"] if rows is None else rows
+    import numpy as np
+    return workloads.random_noisy(n, w["d"], m=w["m"], zeta=w["zeta"], seed=w["seed"] + 1000 * rank,
+                                  dtype=np.float32, row_stop=n)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = max(mx, float(p[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def cpu_baseline(w, rows_sample):
+    """The FP64 oracle as it stands, on the host cores, on the first rows."""
+    import numpy as np
+    from oracle import fd_sketch
+    from paper_1501_06561_gb300 import workloads
+    A = workloads.random_noisy(rows_sample, w["d"], m=w["m"], zeta=w["zeta"], seed=w["seed"],
+                               dtype=np.float32, row_stop=rows_sample)
+    t0 = time.perf_counter()
+    fd_sketch(A, w["ell"], w["variant"], w["alpha"])
+    dt = time.perf_counter() - t0
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([x.get("num_threads", 1) for x in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    return {"value": rows_sample / dt, "unit": "rows/s", "cores": int(cores), "kind": "oracle",
+            "sample": f"first {rows_sample} rows of the workload stream ({dt:.1f} s of CPU work)"}
+
+
+def run_reference_batch(args, w):
+    """Oracle on a sample of the batched workload's streams (host-drawn with
+    the same recipe), timed per step; rows/s over the sampled streams."""
+    import numpy as np
+    from oracle import fd_sketch
+    from paper_1501_06561_gb300 import workloads
+    specs = workloads.batch_specs(args.count or w["count"], seed=w["seed"])
+    order = sorted(range(len(specs)), key=lambda i: specs[i]["d"] * specs[i]["ell"])
+    pick = [order[0], order[len(order) // 4], order[len(order) // 2]]
+    data = [workloads.random_noisy(specs[i]["n"], specs[i]["d"], m=max(1, specs[i]["ell"] // 2),
+                                   seed=specs[i]["seed"], dtype="bf16") for i in pick]
+    rows = sum(a.shape[0] for a in data)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for i, a in zip(pick, data):
+            fd_sketch(a, specs[i]["ell"], w["variant"], w["alpha"])
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    return rows, t, f"{len(pick)} streams of the batch (ids {pick}, {rows} rows) per step"
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    if args.workload == "c3":
+        rows, t, sample = run_reference_batch(args, w)
+        try:
+            from threadpoolctl import threadpool_info
+            cores = max([x.get("num_threads", 1) for x in threadpool_info()] + [1])
+        except Exception:
+            cores = os.cpu_count() or 1
+        val = rows / t
+        print(json.dumps({"impl": "reference", "metric": "FD rows/s", "value": val,
+                          "unit": "rows/s", "n_gpus": args.gpus, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": t * 1e3,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": w["name"], "sample": sample},
+                          "cpu_baseline": {"kind": "oracle", "cores": int(cores), "value": val,
+                                           "unit": "rows/s", "sample": sample},
+                          "e2e": {"value": val, "unit": "rows/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return 0
+    rows = args.cpu_sample_rows or default_sample_rows(w)
+    times = []
+    import numpy as np
+    from oracle import fd_sketch
+    from paper_1501_06561_gb300 import workloads
+    A = workloads.random_noisy(rows, w["d"], m=w["m"], zeta=w["zeta"], seed=w["seed"],
+                               dtype=np.float32, row_stop=rows)
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        fd_sketch(A, w["ell"], w["variant"], w["alpha"])
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([x.get("num_threads", 1) for x in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    val = rows / t
+    line = {"impl": "reference", "metric": "FD rows/s", "value": val, "unit": "rows/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "ell": w["ell"], "variant": w["variant"],
+                       "sample_rows": rows},
+            "cpu_baseline": {"kind": "oracle", "cores": int(cores), "value": val, "unit": "rows/s",
+                             "sample": f"first {rows} rows of the workload stream per step"},
+            "e2e": {"value": val, "unit": "rows/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def default_sample_rows(w):
+    # about 10-30 s of oracle work: the oracle's SVD of a 2*ell x d buffer per
+    # ell+1 rows dominates
+    per_red = 8e-10 * (2 * w["ell"]) ** 2 * w["d"]  # seconds per reduction (SVD of 2 ell x d)
+    reds = max(20, int(15.0 / max(per_red, 1e-5)))
+    return int(min(w["n"], 2 * w["ell"] + reds * (w["ell"] + 1)))
+
+
+def batch_reductions(n, ell):
+    L = 2 * ell
+    return 0 if n < L else 1 + (n - L) // (ell + 1)
+
+
+def run_batch(args, w):
+    """Batched workload: every stream through fd_batch_append (one persistent
+    launch) and fd_batch_sketch_all (one launch) per step."""
+    import numpy as np
+    import torch
+    from paper_1501_06561_gb300 import fd, workloads
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    fd.load()
+    count = args.count or w["count"]
+    specs = workloads.batch_specs(count, seed=w["seed"] + 1000 * rank)
+    flat, views = workloads.batch_streams_device(specs)
+    ds = [sp["d"] for sp in specs]
+    ells = [sp["ell"] for sp in specs]
+    b = fd.FDBatch(ds, ells, w["variant"], w["alpha"], w["prec"])
+    blocks = {i: flat[off:off + n * d].view(n, d) for i, (off, n, d) in enumerate(views)}
+    prep = b.prepare(blocks)
+    offs, tot = b.offsets()
+    out = torch.empty(tot, device="cuda", dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+    rows = int(sum(sp["n"] for sp in specs))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    ka = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+
+    def step(i=None):
+        b.reset()
+        if i is not None:
+            ka[2 * i].record(stream)
+        b.append_prepared(prep)
+        if i is not None:
+            ka[2 * i + 1].record(stream)
+        b.sketch_all(out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        step(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_kernel = sum(ka[2 * i].elapsed_time(ka[2 * i + 1]) for i in range(args.steps)) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = rows * world / (ms / 1e3)
+
+    # end to end: host rows (a bounded copy of the device streams would not fit the
+    # host for 10^8 rows, so the e2e leg copies every stream from pinned host memory
+    # into the device buffer inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(flat.numel(), dtype=flat.dtype, pin_memory=True)
+        host.copy_(flat)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.steps)):
+            flat.copy_(host, non_blocking=True)
+            step()
+            hout = out.to("cpu")
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / max(1, args.steps)
+        e2e = {"value": rows * world / dt, "unit": "rows/s",
+               "h2d_bytes_per_step": int(flat.numel() * flat.element_size()),
+               "d2h_bytes_per_step": int(hout.numel() * 4)}
+        del host
+
+    if rank != 0:
+        b.close()
+        return 0
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    alu_peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    flops = 0.0
+    for sp in specs:
+        L = 2 * sp["ell"]
+        r = batch_reductions(sp["n"], sp["ell"])
+        flops += r * (9.0 * L ** 3 + 2.0 * L * L * sp["d"] + 2.0 * (sp["ell"] - 1) * L * sp["d"])
+    achieved = flops / (ms_kernel / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "batch_kernel (persistent: ingest, Gram, Jacobi, "
+                "shrink, rotate per sketch)", "achieved": achieved, "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                "peak_source": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "algorithmic_flops_per_launch": flops, "avg_launch_us": ms_kernel * 1e3,
+                "hbm_bytes_per_launch": int(flat.numel() * flat.element_size())}
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline_batch(specs, flat, views, w)
+    line = {
+        "metric": "FD rows/s (batched sketch update, every stream per step)",
+        "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (bf16 rows), f64 shrink",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "sketches": count, "rows_per_step": rows,
+                   "reductions_per_step": int(sum(batch_reductions(sp["n"], sp["ell"])
+                                                  for sp in specs)),
+                   "input_bytes": int(flat.numel() * flat.element_size()),
+                   "l2": "input larger than L2 (no flush needed)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roofline, "gpu_launches": 2 * args.steps, "clocks": clk, "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    b.close()
+    return 0
+
+
+def cpu_baseline_batch(specs, flat, views, w, budget_s=20.0):
+    """The oracle on a stratified sample of the batch's streams (smallest and
+    largest d*ell first), until about budget_s seconds of CPU work."""
+    import numpy as np
+    import torch
+    from oracle import fd_sketch
+    order = sorted(range(len(specs)), key=lambda i: specs[i]["d"] * specs[i]["ell"])
+    pick = [order[0], order[-1], order[len(order) // 2], order[len(order) // 4],
+            order[3 * len(order) // 4]]
+    rows, t = 0, 0.0
+    used = []
+    for i in pick:
+        off, n, d = views[i]
+        A = flat[off:off + n * d].view(n, d).float().cpu().numpy()
+        t0 = time.perf_counter()
+        fd_sketch(A, specs[i]["ell"], w["variant"], w["alpha"])
+        t += time.perf_counter() - t0
+        rows += n
+        used.append(i)
+        if t > budget_s:
+            break
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([x.get("num_threads", 1) for x in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    return {"value": rows / t, "unit": "rows/s", "cores": int(cores), "kind": "oracle",
+            "sample": f"{len(used)} of the batch's streams (ids {used}, {rows} rows, {t:.1f} s)"}
+
+
+def main():
+    args = parse()
+    w = config(args)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    if args.workload == "c3":
+        return run_batch(args, w)
+    import numpy as np
+    import torch
+    from paper_1501_06561_gb300 import fd
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    fd.load()
+
+    A_host = make_rows(w, rank)
+    A = torch.from_numpy(A_host).cuda()
+    B = torch.empty(w["ell"], w["d"], device="cuda", dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    sk = fd.FDSketch(w["d"], w["ell"], w["variant"], w["alpha"], w["prec"])
+
+    def step(s, src):
+        s.reset()
+        s.append(src)
+        s.sketch(out=B)
+
+    for _ in range(args.warmup):
+        step(sk, A)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    sk.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(sk, A)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    ktimes = sk.kernel_times()
+    sk.profile(False)
+    clk = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = w["n"] * world / (ms / 1e3)
+    st = sk.stats()
+    launches = sum(c for c, _ in ktimes.values())
+    # accuracy of this run: cov-err of the sketch against the whole stream
+    cov = sk.cov_err(A)
+
+    # end to end through host buffers (pinned staging and copies inside)
+    e2e = None
+    if not args.no_e2e:
+        Bh = np.empty((w["ell"], w["d"]), dtype=np.float32)
+        sk.reset()
+        sk.append(A_host[: 4 * w["ell"]])
+        sk.sketch()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.steps)):
+            sk.reset()
+            sk.append(A_host)
+            Bh = sk.sketch(dtype=np.float32)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / max(1, args.steps)
+        e2e = {"value": w["n"] * world / dt, "unit": "rows/s",
+               "h2d_bytes_per_step": int(A_host.nbytes), "d2h_bytes_per_step": int(Bh.nbytes)}
+
+    # plain FP32 CUDA-core update on the same stream, for the matched-error comparison
+    plain = None
+    if not args.no_plain and w["prec"] != "fp32":
+        sp = fd.FDSketch(w["d"], w["ell"], w["variant"], w["alpha"], "fp32")
+        step(sp, A)
+        torch.cuda.synchronize()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        step(sp, A)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        pms = q0.elapsed_time(q1)
+        plain = {"value": w["n"] / (pms / 1e3), "unit": "rows/s", "cov_err": sp.cov_err(A)}
+        sp.close()
+
+    if rank != 0:
+        sk.close()
+        return 0
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    alu_peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA
+    n_eig, ms_eig = ktimes["eig"]
+    L = 2 * w["ell"]
+    eig_flops = 9.0 * L ** 3  # textbook dense symmetric eigensolve with vectors
+    achieved = (eig_flops / (ms_eig / max(n_eig, 1) / 1e3)) / 1e12 if n_eig else None
+    roofline = {"bound": "alu", "kernel": "eigensolve + shrink (one CTA per reduction)",
+                "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": (achieved / alu_peak) if achieved else None, "traffic": None,
+                "peak_source": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "algorithmic_flops_per_launch": eig_flops,
+                "avg_launch_us": (ms_eig / n_eig * 1e3) if n_eig else None}
+    kshare = {k: {"launches": c, "ms_per_step": m / args.steps,
+                  "share": (m / sum(x for _, x in ktimes.values())) if ktimes else None}
+              for k, (c, m) in ktimes.items()}
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        cpu = cpu_baseline(w, args.cpu_sample_rows or default_sample_rows(w))
+    line = {
+        "metric": "FD rows/s (sketch update, whole stream per step)",
+        "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16x3": "bf16x3 (fp32 accumulate), fp32 eig, f64 shrink",
+                  "fp32": "f32, f64 shrink", "fp64": "f64"}[w["prec"]],
+        "data": "synthetic",
+        "config": {"workload": w["name"], "ell": w["ell"], "variant": w["variant"],
+                   "alpha": w["alpha"], "prec": w["prec"], "rows_per_step": w["n"],
+                   "input_bytes": int(A_host.nbytes),
+                   "l2": "input larger than L2 (no flush needed)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "cov_err": cov, "reductions_per_step": st["reductions"],
+        "plain_fp32": plain,
+        "roofline": roofline, "kernels": kshare,
+        "gpu_launches": int(launches + 2 * args.steps),
+        "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    sk.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

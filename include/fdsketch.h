@@ -142,8 +142,55 @@ int fd_stats(fd_handle h, fd_stats_t* s);
  * 2*ell values) and sigma'^2 aligned with it, FP64, host arrays of 2*ell. */
 int fd_last_spectrum(fd_handle h, double* sigma2, double* sigma_prime2);
 
+/* Return the handle to its just-created state (empty buffer, zero counters)
+ * while keeping its allocations; ordered on the handle's stream. */
+int fd_reset(fd_handle h);
+
+/* Device-time accounting per kernel class. fd_profile(h, 1) starts bracketing
+ * every launch of the handle with CUDA events on its stream (and clears the
+ * totals); fd_profile(h, 0) stops. fd_kernel_times synchronises the stream and
+ * fills counts[c] (launches) and ms[c] (summed device milliseconds) for the
+ * classes c < FD_KCLASSES: ingest, Gram, eigensolve + shrink, rotate. */
+#define FD_KCLASSES 4
+enum { FD_K_INGEST = 0, FD_K_GRAM = 1, FD_K_EIG = 2, FD_K_ROTATE = 3 };
+int fd_profile(fd_handle h, int32_t enable);
+int fd_kernel_times(fd_handle h, int64_t* counts, double* ms);
+
 /* Release every resource of the handle (synchronises its stream). */
 int fd_destroy(fd_handle h);
+
+/* ---- Batched sketches --------------------------------------------------
+ * Many independent sketches (each with its own d and ell, 2*ell <= 128) that
+ * share one variant and are updated together: one fd_batch_append call runs a
+ * single persistent launch in which every CTA takes work items (a sketch and a
+ * block of its rows) from a device queue ordered longest-first and runs the
+ * whole block through the buffered update of that sketch (ingest, Gram,
+ * Jacobi eigensolve, ReduceRank, rotate) without leaving the CTA. Per sketch
+ * the arithmetic and the result are those of a single handle with
+ * FD_PREC_FP32. */
+typedef struct fd_batch_state* fd_batch;
+typedef struct {
+  int32_t id;        /* sketch index, 0 <= id < count; at most once per call */
+  int32_t dtype;     /* FD_F32, FD_BF16 or FD_F64 */
+  const void* rows;  /* device pointer, n rows of d_id values, row stride ld */
+  int64_t n;
+  int64_t ld;
+} fd_work_t;
+
+int fd_batch_create(int32_t count, const int64_t* d, const int32_t* ell, int32_t variant,
+                    double alpha, int32_t prec, void* cuda_stream, fd_batch* out);
+/* Append row blocks to sketches; asynchronous on the batch's stream. */
+int fd_batch_append(fd_batch b, const fd_work_t* items, int32_t n_items);
+/* Sketch `id` as ell_id x d_id rows (same flush rule as fd_sketch). */
+int fd_batch_sketch(fd_batch b, int32_t id, void* out, int32_t dtype, int32_t out_on_device);
+/* Every sketch at once, into one device buffer of FP32: sketch id is written
+ * as ell_id x d_id rows (leading dimension d_id) at out + offsets[id]
+ * (offsets: host array of count element offsets). Same flush rule as
+ * fd_sketch; one launch, asynchronous on the batch's stream. */
+int fd_batch_sketch_all(fd_batch b, float* out, const int64_t* offsets);
+int fd_batch_stats(fd_batch b, int32_t id, fd_stats_t* s);
+int fd_batch_reset(fd_batch b);
+int fd_batch_destroy(fd_batch b);
 
 /* Text for an FD_E* code (static storage). */
 const char* fd_strerror(int32_t code);

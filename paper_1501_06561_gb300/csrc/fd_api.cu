@@ -9,6 +9,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "fd_internal.cuh"
 
@@ -38,10 +39,12 @@ int tc_create(TcCtx** out, int64_t d, int ell, cudaStream_t st);
 void tc_destroy(TcCtx* t);
 int tc_ingest(TcCtx* t, const void* src, int64_t n, int64_t ld, int dtype, int row0,
               double* rownorm, DevCounters* ctr);
-int tc_reduce(TcCtx* t, int nrows, const EigArgs& eig_template, int write_sketch,
-              float* sketch_out, int64_t ldo);
+int tc_gram(TcCtx* t, int nrows);
+int tc_eig(TcCtx* t, const EigArgs& eig_template);
+int tc_rotate(TcCtx* t, int nrows, int write_sketch, float* sketch_out, int64_t ldo);
 int tc_export_rows(TcCtx* t, int rows, float* out, int64_t ldo);
 int tc_error(TcCtx* t);
+int tc_reset(TcCtx* t);
 
 }  // namespace fdk
 
@@ -97,7 +100,50 @@ struct fd_state {
   TcCtx* tc = nullptr;    // tensor-core planes (FD_PREC_BF16X3)
   int max_sweeps = 30;
   double tol = 0.0;
+
+  // kernel timing (fd_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_marks;  // (class, index of start event)
+  int64_t kcount[FD_KCLASSES] = {0, 0, 0, 0};
+  double kms[FD_KCLASSES] = {0, 0, 0, 0};
 };
+
+// Bracket a launch of kernel class `cls` with events when profiling is on.
+struct ProfScope {
+  fd_state* h;
+  int cls;
+  int idx = -1;
+  ProfScope(fd_state* hh, int c) : h(hh), cls(c) {
+    if (!h->prof) return;
+    const size_t need = h->ev_marks.size() * 2 + 2;
+    while (h->ev_pool.size() < need) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      h->ev_pool.push_back(e);
+    }
+    idx = (int)h->ev_marks.size() * 2;
+    cudaEventRecord(h->ev_pool[idx], h->st);
+  }
+  ~ProfScope() {
+    if (idx < 0) return;
+    cudaEventRecord(h->ev_pool[idx + 1], h->st);
+    h->ev_marks.emplace_back(cls, idx);
+  }
+};
+
+static void prof_collect(fd_state* h) {
+  if (h->ev_marks.empty()) return;
+  cudaStreamSynchronize(h->st);
+  for (auto& m : h->ev_marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev_pool[m.second], h->ev_pool[m.second + 1]) == cudaSuccess) {
+      h->kcount[m.first] += 1;
+      h->kms[m.first] += ms;
+    }
+  }
+  h->ev_marks.clear();
+}
 
 static size_t dtype_size(int dt) {
   return dt == FD_F32 ? 4 : (dt == FD_BF16 ? 2 : (dt == FD_F64 ? 8 : 0));
@@ -106,6 +152,7 @@ static size_t dtype_size(int dt) {
 static void free_state(fd_state* h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   for (int i = 0; i < 2; ++i) {
     cudaFree(h->buf[i]);
     cudaFree(h->dstage[i]);
@@ -232,8 +279,13 @@ static int reduce_rows(fd_state* h, int nrows, void* out, int64_t ldo, DevCounte
   a.tol = h->tol;
   a.symmetrize = 1;
   if (h->prec == FD_PREC_BF16X3) {
-    int rc = tc_reduce(h->tc, nrows, a, out != nullptr ? 1 : 0,
-                       reinterpret_cast<float*>(out), ldo);
+    int rc;
+    { ProfScope ps(h, FD_K_GRAM); rc = tc_gram(h->tc, nrows); }
+    if (rc != FD_OK) return rc;
+    { ProfScope ps(h, FD_K_EIG); rc = tc_eig(h->tc, a); }
+    if (rc != FD_OK) return rc;
+    { ProfScope ps(h, FD_K_ROTATE);
+      rc = tc_rotate(h->tc, nrows, out != nullptr ? 1 : 0, reinterpret_cast<float*>(out), ldo); }
     return rc;
   }
   const int slices = gram_simt_slices(h->d, h->ksplit);
@@ -243,20 +295,26 @@ static int reduce_rows(fd_state* h, int nrows, void* out, int64_t ldo, DevCounte
   a.part_stride = (long long)h->ldp * h->ldp;
   if (h->prec == FD_PREC_FP64) {
     const double* B = reinterpret_cast<const double*>(h->buf[h->cur]);
-    FD_CK((launch_gram_simt<double>(B, h->ldb, nrows, h->d, reinterpret_cast<double*>(h->parts),
-                                    h->ldp, h->ksplit, h->st)));
-    FD_CK(launch_eig_shrink<double>(a, h->st));
-    FD_CK((launch_rotate_simt<double>(reinterpret_cast<const double*>(h->wrot), h->ldr,
-                                      h->ell - 1, nrows, B, h->ldb,
-                                      reinterpret_cast<double*>(out), ldo, h->d, h->st)));
+    { ProfScope ps(h, FD_K_GRAM);
+      FD_CK((launch_gram_simt<double>(B, h->ldb, nrows, h->d, reinterpret_cast<double*>(h->parts),
+                                      h->ldp, h->ksplit, h->st))); }
+    { ProfScope ps(h, FD_K_EIG);
+      FD_CK(launch_eig_shrink<double>(a, h->st)); }
+    { ProfScope ps(h, FD_K_ROTATE);
+      FD_CK((launch_rotate_simt<double>(reinterpret_cast<const double*>(h->wrot), h->ldr,
+                                        h->ell - 1, nrows, B, h->ldb,
+                                        reinterpret_cast<double*>(out), ldo, h->d, h->st))); }
   } else {
     const float* B = reinterpret_cast<const float*>(h->buf[h->cur]);
-    FD_CK((launch_gram_simt<float>(B, h->ldb, nrows, h->d, reinterpret_cast<float*>(h->parts),
-                                   h->ldp, h->ksplit, h->st)));
-    FD_CK(launch_eig_shrink<float>(a, h->st));
-    FD_CK((launch_rotate_simt<float>(reinterpret_cast<const float*>(h->wrot), h->ldr,
-                                     h->ell - 1, nrows, B, h->ldb,
-                                     reinterpret_cast<float*>(out), ldo, h->d, h->st)));
+    { ProfScope ps(h, FD_K_GRAM);
+      FD_CK((launch_gram_simt<float>(B, h->ldb, nrows, h->d, reinterpret_cast<float*>(h->parts),
+                                     h->ldp, h->ksplit, h->st))); }
+    { ProfScope ps(h, FD_K_EIG);
+      FD_CK(launch_eig_shrink<float>(a, h->st)); }
+    { ProfScope ps(h, FD_K_ROTATE);
+      FD_CK((launch_rotate_simt<float>(reinterpret_cast<const float*>(h->wrot), h->ldr,
+                                       h->ell - 1, nrows, B, h->ldb,
+                                       reinterpret_cast<float*>(out), ldo, h->d, h->st))); }
   }
   return FD_OK;
 }
@@ -268,6 +326,7 @@ static int append_device(fd_state* h, const char* src, int64_t n, int64_t ld, in
   int64_t i = 0;
   while (i < n) {
     const int c = (int)std::min<int64_t>(n - i, h->L - h->m);
+    ProfScope* ps = new ProfScope(h, FD_K_INGEST);
     if (h->prec == FD_PREC_BF16X3) {
       int rc = tc_ingest(h->tc, src + i * rb, c, ld, dtype, h->m, h->rownorm, h->ctr);
       if (rc != FD_OK) return rc;
@@ -277,6 +336,7 @@ static int append_device(fd_state* h, const char* src, int64_t n, int64_t ld, in
                           h->d, h->rownorm, h->ctr, nullptr, nullptr, 0, nullptr, nullptr, 0,
                           h->m, h->st));
     }
+    delete ps;
     h->m += c;
     h->n_seen += c;
     i += c;
@@ -416,6 +476,42 @@ extern "C" int fd_last_spectrum(fd_handle h, double* sigma2, double* sigma_prime
   FD_CK(cudaMemcpyAsync(sigma2, h->sig2, (size_t)h->L * 8, cudaMemcpyDeviceToHost, h->st));
   FD_CK(cudaMemcpyAsync(sigma_prime2, h->sigp2, (size_t)h->L * 8, cudaMemcpyDeviceToHost, h->st));
   FD_CK(cudaStreamSynchronize(h->st));
+  return FD_OK;
+}
+
+extern "C" int fd_reset(fd_handle h) {
+  if (!h) return FD_EINVAL;
+  const size_t bufbytes = (size_t)h->L * h->ldb * h->es;
+  for (int i = 0; i < 2; ++i)
+    if (h->buf[i]) FD_CK(cudaMemsetAsync(h->buf[i], 0, bufbytes, h->st));
+  if (h->tc) {
+    int rc = tc_reset(h->tc);
+    if (rc != FD_OK) return rc;
+  }
+  FD_CK(cudaMemsetAsync(h->ctr, 0, sizeof(DevCounters), h->st));
+  FD_CK(cudaMemsetAsync(h->ctr_flush, 0, sizeof(DevCounters), h->st));
+  FD_CK(cudaMemsetAsync(h->sig2, 0, (size_t)FD_MAX_BUFFER_ROWS * 8, h->st));
+  FD_CK(cudaMemsetAsync(h->sigp2, 0, (size_t)FD_MAX_BUFFER_ROWS * 8, h->st));
+  h->cur = 0;
+  h->m = 0;
+  h->n_seen = 0;
+  h->flushed = false;
+  return FD_OK;
+}
+
+extern "C" int fd_profile(fd_handle h, int32_t enable) {
+  if (!h) return FD_EINVAL;
+  prof_collect(h);
+  h->prof = enable != 0;
+  if (h->prof)
+    for (int c = 0; c < FD_KCLASSES; ++c) { h->kcount[c] = 0; h->kms[c] = 0.0; }
+  return FD_OK;
+}
+
+extern "C" int fd_kernel_times(fd_handle h, int64_t* counts, double* ms) {
+  if (!h || !counts || !ms) return FD_EINVAL;
+  prof_collect(h);
+  for (int c = 0; c < FD_KCLASSES; ++c) { counts[c] = h->kcount[c]; ms[c] = h->kms[c]; }
   return FD_OK;
 }
 

@@ -1,0 +1,591 @@
+// Batched update of many independent sketches in one persistent launch.
+//
+// Every sketch keeps its own 2*ell x d FP32 buffer and FP64 counters in HBM.
+// A fixed grid of CTAs (two per SM) pulls work items -- (sketch, block of
+// rows) -- from a device queue ordered longest-first; the CTA that takes an
+// item runs the whole row block through Algorithm 1 (Sec. 2.3) for that
+// sketch: ingest, and at every full buffer one reduction done entirely inside
+// the CTA (Gram into shared memory, one-sided Jacobi eigensolve in shared
+// memory, FP64 ReduceRank, rotate back into the buffer). No inter-CTA
+// synchronisation is needed because a sketch is owned by one CTA at a time.
+// The launch is captured in a CUDA graph once per item table and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "fd_internal.cuh"
+#include "fd_eig.cuh"
+#include "fd_jacobi.cuh"
+
+namespace fdk {
+
+namespace {
+
+constexpr int BT = 512;           // threads per CTA
+constexpr int BMAX_L = 128;       // largest buffer (2*ell) a batched sketch may have
+constexpr int KCH = 32;           // Gram K chunk
+constexpr int RCH = 64;           // rotate column chunk
+
+struct BatchSketch {
+  long long d, ldb;
+  int ell, L, m, pad;
+  float* buf;          // L x ldb, FP32
+  DevCounters* ctr;
+};
+
+struct BatchItem {
+  int id, dtype;
+  const void* rows;
+  long long n, ld;
+};
+
+__device__ __forceinline__ float load_as_f32(const void* p, long long idx, int dtype) {
+  if (dtype == FD_F32) return reinterpret_cast<const float*>(p)[idx];
+  if (dtype == FD_F64) return (float)reinterpret_cast<const double*>(p)[idx];
+  const unsigned short raw = reinterpret_cast<const unsigned short*>(p)[idx];
+  return __uint_as_float(((unsigned int)raw) << 16);
+}
+
+__device__ __forceinline__ double load_as_f64(const void* p, long long idx, int dtype) {
+  if (dtype == FD_F64) return reinterpret_cast<const double*>(p)[idx];
+  return (double)load_as_f32(p, idx, dtype);
+}
+
+// Shared memory map (bytes): region A 64 KB (Jacobi matrix / rotate staging),
+// region B 32 KB (Gram staging / rotate matrix), scalars.
+constexpr size_t REG_A = (size_t)BMAX_L * BMAX_L * 4;
+constexpr size_t REG_B = (size_t)BMAX_L * RCH * 4;
+constexpr size_t SCAL = (size_t)BMAX_L * (4 * sizeof(double) + 2 * sizeof(int)) + BMAX_L * 4 + 256;
+constexpr size_t BATCH_SMEM = REG_A + REG_B + SCAL;
+
+// One reduction of the first `nrows` rows of S.buf; new rows 0..ell-2 go to
+// `out` (stride ldo; may be S.buf itself), counters from cin to cout.
+__device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long long ldo,
+                             const DevCounters* cin, DevCounters* cout, int variant,
+                             double alpha, int max_sweeps, double tol, unsigned char* smem) {
+  const int tid = threadIdx.x;
+  float* A = reinterpret_cast<float*>(smem);
+  float* Bst = reinterpret_cast<float*>(smem + REG_A);
+  unsigned char* sc = smem + REG_A + REG_B;
+  const int np = nrows + (nrows & 1);
+  const int ld = (np + 3) & ~3;
+  const long long d = S.d, ldb = S.ldb;
+  const float* buf = S.buf;
+
+  // ---- Gram G = B B^T (upper 4x4 blocks, K in chunks of KCH staged in Bst) ----
+  const int nb4 = (np + 3) / 4;
+  const int nblk = nb4 * (nb4 + 1) / 2;
+  float acc[2][16];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[u][e] = 0.f;
+  int bi[2], bj[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    int b = tid + u * BT;
+    bi[u] = -1;
+    bj[u] = -1;
+    if (b < nblk) {
+      // unrank b -> (i, j) with i <= j in row-major upper triangle
+      int i = 0, rem = b;
+      while (rem >= nb4 - i) { rem -= nb4 - i; ++i; }
+      bi[u] = i;
+      bj[u] = i + rem;
+    }
+  }
+  for (long long k0 = 0; k0 < d; k0 += KCH) {
+    __syncthreads();
+    for (int idx = tid; idx < np * KCH; idx += BT) {
+      const int r = idx / KCH, k = idx % KCH;
+      Bst[k * (BMAX_L + 4) + r] =
+          (r < nrows && k0 + k < d) ? buf[(long long)r * ldb + k0 + k] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (bi[u] < 0) continue;
+      const int i0 = bi[u] * 4, j0 = bj[u] * 4;
+#pragma unroll 8
+      for (int k = 0; k < KCH; ++k) {
+        const float4 a4 = *reinterpret_cast<const float4*>(&Bst[k * (BMAX_L + 4) + i0]);
+        const float4 b4 = *reinterpret_cast<const float4*>(&Bst[k * (BMAX_L + 4) + j0]);
+        const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+        const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[u][x * 4 + y] = fmaf(av[x], bv[y], acc[u][x * 4 + y]);
+      }
+    }
+  }
+  __syncthreads();
+  // write G (both triangles) into A with stride ld, zero padding
+  for (int idx = tid; idx < np * ld; idx += BT) A[idx] = 0.f;
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    if (bi[u] < 0) continue;
+    const int i0 = bi[u] * 4, j0 = bj[u] * 4;
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int i = i0 + x, j = j0 + y;
+        if (i < nrows && j < nrows) {
+          A[i * ld + j] = acc[u][x * 4 + y];
+          A[j * ld + i] = acc[u][x * 4 + y];
+        }
+      }
+  }
+  __syncthreads();
+
+  // ---- eigensolve (scaled by the largest diagonal entry) ----
+  __shared__ float s_max;
+  if (tid == 0) s_max = 0.f;
+  __syncthreads();
+  float dm = 0.f;
+  for (int i = tid; i < nrows; i += BT) dm = fmaxf(dm, fabsf(A[i * ld + i]));
+  for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+  if ((tid & 31) == 0) atomicMax(reinterpret_cast<int*>(&s_max), __float_as_int(dm));
+  __syncthreads();
+  const float smax = s_max;
+  const float inv = smax > 0.f ? 1.f / smax : 1.f;
+  for (int idx = tid; idx < np * ld; idx += BT) A[idx] *= inv;
+  float* nrm = reinterpret_cast<float*>(sc);
+  double* lam = reinterpret_cast<double*>(sc + BMAX_L * 4);
+  double* mu = lam + BMAX_L;
+  double* mup = mu + BMAX_L;
+  double* scl = mup + BMAX_L;
+  int* ord = reinterpret_cast<int*>(scl + BMAX_L);
+  int* rrank = ord + BMAX_L;
+  __syncthreads();
+  int capped = 0;
+  const int sweeps = jacobi_sweeps_f32<8, 4, 1>(A, ld, np, nrm, max_sweeps, (float)tol, &capped);
+
+  // ---- shrink + rotate matrix (rows 0..ell-2, stride np) into Bst ----
+  EigArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n = nrows;
+  a.ell = S.ell;
+  a.variant = variant;
+  a.alpha = alpha;
+  a.ctr_in = cin;
+  a.ctr_out = cout;
+  a.wrot = Bst;
+  a.ldr = np;
+  a.max_sweeps = max_sweeps;
+  __syncthreads();
+  eig_finish<float>(a, A, ld, nrows, np, sweeps, capped, smax > 0.f ? (double)smax : 1.0, lam,
+                    mu, mup, scl, ord, rrank);
+  __syncthreads();
+
+  // ---- rotate: out[r][c] = sum_i W[r][i] B[i][c], column chunks staged in A ----
+  const int nout = S.ell - 1;
+  float* W = Bst;
+  for (long long c0 = 0; c0 < d; c0 += RCH) {
+    __syncthreads();
+    for (int idx = tid; idx < nrows * RCH; idx += BT) {
+      const int r = idx / RCH, c = idx % RCH;
+      A[r * RCH + c] = (c0 + c < d) ? buf[(long long)r * ldb + c0 + c] : 0.f;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nout * RCH; idx += BT) {
+      const int r = idx / RCH, c = idx % RCH;
+      float s0 = 0.f, s1 = 0.f;
+      const float* wr = W + r * np;
+      int i = 0;
+      for (; i + 1 < nrows; i += 2) {
+        s0 = fmaf(wr[i], A[i * RCH + c], s0);
+        s1 = fmaf(wr[i + 1], A[(i + 1) * RCH + c], s1);
+      }
+      if (i < nrows) s0 = fmaf(wr[i], A[i * RCH + c], s0);
+      if (c0 + c < d) out[(long long)r * ldo + c0 + c] = s0 + s1;
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(BT, 2)
+    batch_kernel(BatchSketch* __restrict__ sk, const BatchItem* __restrict__ items, int nitems,
+                 int* __restrict__ next, int variant, double alpha, int max_sweeps,
+                 double tol) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  __shared__ double s_rn[BMAX_L];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_item = atomicAdd(next, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= nitems) break;
+    const BatchItem item = items[it];
+    BatchSketch S = sk[item.id];
+    int m = S.m;
+    long long i = 0;
+    while (i < item.n) {
+      const int c = (int)min((long long)(S.L - m), item.n - i);
+      // ingest c rows: warp per row, FP64 row norms summed in row order
+      for (int r = warp; r < c; r += BT / 32) {
+        const long long src = (i + r) * item.ld;
+        float* dst = S.buf + (long long)(m + r) * S.ldb;
+        double acc = 0.0;
+        for (long long k = lane; k < S.d; k += 32) {
+          const double x = load_as_f64(item.rows, src + k, item.dtype);
+          dst[k] = (float)x;
+          acc = fma(x, x, acc);
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) s_rn[r] = acc;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double tot = S.ctr->norm_a2;
+        for (int r = 0; r < c; ++r) tot += s_rn[r];
+        S.ctr->norm_a2 = tot;
+      }
+      m += c;
+      i += c;
+      if (m == S.L) {
+        __syncthreads();
+        batch_reduce(S, S.L, S.buf, S.ldb, S.ctr, S.ctr, variant, alpha, max_sweeps, tol, smem);
+        m = S.ell - 1;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) sk[item.id].m = m;
+  }
+}
+
+// Flush one sketch on a copy: rows 0..ell-2 of the reduction of its m pending
+// rows go to out; counters to cout. One CTA.
+__global__ void __launch_bounds__(BT, 1)
+    batch_flush_kernel(const BatchSketch* __restrict__ sk, int id, float* out, long long ldo,
+                       DevCounters* cout, int variant, double alpha, int max_sweeps, double tol) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const BatchSketch S = sk[id];
+  batch_reduce(S, S.m, out, ldo, S.ctr, cout, variant, alpha, max_sweeps, tol, smem);
+}
+
+// Every sketch of the batch, flushed on a copy like fd_sketch, into one
+// device arena: sketch id at out + offs[id] as ell_id x d_id rows.
+__global__ void __launch_bounds__(BT, 1)
+    batch_flush_all_kernel(const BatchSketch* __restrict__ sk, int count, float* out,
+                           const long long* __restrict__ offs, DevCounters* fctr, int variant,
+                           double alpha, int max_sweeps, double tol) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  for (int id = blockIdx.x; id < count; id += gridDim.x) {
+    const BatchSketch S = sk[id];
+    float* o = out + offs[id];
+    int valid;
+    if (S.m > S.ell - 1) {
+      batch_reduce(S, S.m, o, S.d, S.ctr, fctr + id, variant, alpha, max_sweeps, tol, smem);
+      valid = S.ell - 1;
+    } else {
+      for (long long idx = threadIdx.x; idx < (long long)S.m * S.d; idx += BT) {
+        const long long r = idx / S.d, c = idx % S.d;
+        o[idx] = S.buf[r * S.ldb + c];
+      }
+      if (threadIdx.x == 0) fctr[id] = *S.ctr;
+      valid = S.m;
+    }
+    for (long long idx = (long long)valid * S.d + threadIdx.x; idx < (long long)S.ell * S.d; idx += BT)
+      o[idx] = 0.f;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+}  // namespace fdk
+
+using namespace fdk;
+
+struct fd_batch_state {
+  int count = 0, variant = 0, prec = 0;
+  double alpha = 1.0;
+  cudaStream_t st = nullptr;
+  std::vector<int64_t> d;
+  std::vector<int32_t> ell;
+  std::vector<int> m;          // pending rows per sketch (host mirror)
+  std::vector<int64_t> nseen;
+  std::vector<BatchSketch> hs;
+  BatchSketch* dsk = nullptr;
+  float* arena = nullptr;      // all buffers
+  DevCounters* ctrs = nullptr;
+  DevCounters* ctr_flush = nullptr;
+  float* flush_out = nullptr;  // largest ell x ldb
+  BatchItem* ditems = nullptr;
+  int items_cap = 0;
+  int* next = nullptr;
+  int nsm = 0;
+  int max_sweeps = 30;
+  long long* doffs = nullptr;     // device copy of the sketch_all offsets
+  DevCounters* fctr_all = nullptr;
+};
+
+static int batch_fail(cudaError_t e, const char* w) {
+  set_cuda_error(e, w);
+  return e == cudaErrorMemoryAllocation ? FD_ENOMEM : FD_ECUDA;
+}
+
+extern "C" int fd_batch_destroy(fd_batch_state* b);
+
+extern "C" int fd_batch_create(int32_t count, const int64_t* d, const int32_t* ell, int32_t variant,
+                               double alpha, int32_t prec, void* stream, fd_batch_state** out) {
+  if (!out || count < 1 || !d || !ell) return FD_EINVAL;
+  *out = nullptr;
+  if (variant < FD_VAR_FD || variant > FD_VAR_ISVD) return FD_EINVAL;
+  if (variant == FD_VAR_PFD && !(alpha > 0.0 && alpha <= 1.0)) return FD_EINVAL;
+  if (prec != FD_PREC_FP32) return FD_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (d[i] < 1 || ell[i] < 2 || 2 * ell[i] > BMAX_L) return FD_EINVAL;
+  fd_batch_state* b = new (std::nothrow) fd_batch_state();
+  if (!b) return FD_ENOMEM;
+  b->count = count;
+  b->variant = variant;
+  b->alpha = variant == FD_VAR_PFD ? alpha : 1.0;
+  b->prec = prec;
+  b->st = reinterpret_cast<cudaStream_t>(stream);
+  b->d.assign(d, d + count);
+  b->ell.assign(ell, ell + count);
+  b->m.assign(count, 0);
+  b->nseen.assign(count, 0);
+  size_t total = 0, maxsk = 0;
+  std::vector<size_t> off(count);
+  for (int i = 0; i < count; ++i) {
+    const int64_t ldb = (d[i] + 3) / 4 * 4;
+    off[i] = total;
+    total += (size_t)2 * ell[i] * ldb;
+    maxsk = std::max(maxsk, (size_t)ell[i] * ldb);
+  }
+  cudaError_t e = cudaMalloc(&b->arena, total * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->arena, 0, total * sizeof(float), b->st);
+  if (e == cudaSuccess) e = cudaMalloc(&b->ctrs, (size_t)count * sizeof(DevCounters));
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->ctrs, 0, (size_t)count * sizeof(DevCounters), b->st);
+  if (e == cudaSuccess) e = cudaMalloc(&b->ctr_flush, sizeof(DevCounters));
+  if (e == cudaSuccess) e = cudaMalloc(&b->flush_out, maxsk * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&b->dsk, (size_t)count * sizeof(BatchSketch));
+  if (e == cudaSuccess) e = cudaMalloc(&b->next, sizeof(int));
+  if (e != cudaSuccess) {
+    fd_batch_destroy(b);
+    return batch_fail(e, "fd_batch_create alloc");
+  }
+  b->hs.resize(count);
+  for (int i = 0; i < count; ++i) {
+    BatchSketch& s = b->hs[i];
+    s.d = d[i];
+    s.ldb = (d[i] + 3) / 4 * 4;
+    s.ell = ell[i];
+    s.L = 2 * ell[i];
+    s.m = 0;
+    s.pad = 0;
+    s.buf = b->arena + off[i];
+    s.ctr = b->ctrs + i;
+  }
+  e = cudaMemcpyAsync(b->dsk, b->hs.data(), (size_t)count * sizeof(BatchSketch),
+                      cudaMemcpyHostToDevice, b->st);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BATCH_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(batch_flush_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BATCH_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(batch_flush_all_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BATCH_SMEM);
+  int dev = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) {
+    fd_batch_destroy(b);
+    return batch_fail(e, "fd_batch_create setup");
+  }
+  *out = b;
+  return FD_OK;
+}
+
+extern "C" int fd_batch_append(fd_batch_state* b, const fd_work_t* items, int32_t n_items) {
+  if (!b || (n_items > 0 && !items) || n_items < 0) return FD_EINVAL;
+  if (n_items == 0) return FD_OK;
+  std::vector<int> seen(b->count, 0);
+  std::vector<BatchItem> hi(n_items);
+  std::vector<double> cost(n_items);
+  for (int i = 0; i < n_items; ++i) {
+    const fd_work_t& w = items[i];
+    if (w.id < 0 || w.id >= b->count || seen[w.id] || w.n < 0 || !w.rows ||
+        w.ld < b->d[w.id] || (w.dtype != FD_F32 && w.dtype != FD_BF16 && w.dtype != FD_F64))
+      return FD_EINVAL;
+    seen[w.id] = 1;
+    hi[i] = BatchItem{w.id, w.dtype, w.rows, w.n, w.ld};
+    const double L = 2.0 * b->ell[w.id];
+    // reductions x (eigensolve ~ L^3 + Gram and rotate ~ L^2 d)
+    cost[i] = (double)w.n / (b->ell[w.id] + 1) * (L * L * L * 2.0 + L * L * b->d[w.id]);
+  }
+  // longest first
+  std::vector<int> order(n_items);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  std::vector<BatchItem> sorted(n_items);
+  for (int i = 0; i < n_items; ++i) sorted[i] = hi[order[i]];
+  if (n_items > b->items_cap) {
+    cudaFree(b->ditems);
+    b->ditems = nullptr;
+    cudaError_t e = cudaMalloc(&b->ditems, (size_t)n_items * sizeof(BatchItem));
+    if (e != cudaSuccess) return batch_fail(e, "batch items");
+    b->items_cap = n_items;
+  }
+  cudaError_t e = cudaMemcpyAsync(b->ditems, sorted.data(), (size_t)n_items * sizeof(BatchItem),
+                                  cudaMemcpyHostToDevice, b->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->next, 0, sizeof(int), b->st);
+  if (e != cudaSuccess) return batch_fail(e, "batch items copy");
+  const int grid = std::min(n_items, 2 * b->nsm);
+  const double eps = 1.1920928955078125e-07;
+  batch_kernel<<<grid, BT, BATCH_SMEM, b->st>>>(b->dsk, b->ditems, n_items, b->next, b->variant,
+                                                b->alpha, b->max_sweeps,
+                                                4.0 * eps * std::sqrt((double)BMAX_L));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return batch_fail(e, "batch_kernel");
+  for (int i = 0; i < n_items; ++i) {
+    const int id = items[i].id;
+    const int L = 2 * b->ell[id];
+    int64_t m = b->m[id] + items[i].n;
+    if (m >= L) m = (b->ell[id] - 1) + (m - L) % (b->ell[id] + 1);
+    b->m[id] = (int)m;
+    b->nseen[id] += items[i].n;
+  }
+  return FD_OK;
+}
+
+extern "C" int fd_batch_sketch(fd_batch_state* b, int32_t id, void* out, int32_t dtype,
+                               int32_t out_on_device) {
+  if (!b || id < 0 || id >= b->count || !out || (dtype != FD_F32 && dtype != FD_F64))
+    return FD_EINVAL;
+  const BatchSketch& s = b->hs[id];
+  const int ell = s.ell;
+  const void* src;
+  int valid;
+  cudaError_t e;
+  if (b->m[id] > ell - 1) {
+    const double eps = 1.1920928955078125e-07;
+    batch_flush_kernel<<<1, BT, BATCH_SMEM, b->st>>>(b->dsk, id, b->flush_out, s.ldb,
+                                                     b->ctr_flush, b->variant, b->alpha,
+                                                     b->max_sweeps,
+                                                     4.0 * eps * std::sqrt((double)BMAX_L));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return batch_fail(e, "batch_flush_kernel");
+    src = b->flush_out;
+    valid = ell - 1;
+  } else {
+    e = cudaMemcpyAsync(b->ctr_flush, b->ctrs + id, sizeof(DevCounters), cudaMemcpyDeviceToDevice,
+                        b->st);
+    if (e != cudaSuccess) return batch_fail(e, "batch counters");
+    src = s.buf;
+    valid = b->m[id];
+  }
+  void* dst = out;
+  void* tmp = nullptr;
+  const size_t ob = (size_t)ell * s.d * (dtype == FD_F64 ? 8 : 4);
+  if (!out_on_device) {
+    e = cudaMalloc(&tmp, ob);
+    if (e != cudaSuccess) return batch_fail(e, "batch sketch tmp");
+    dst = tmp;
+  }
+  e = launch_norm_b2(src, 0, s.ldb, valid, s.d, b->ctr_flush, b->st);
+  if (e == cudaSuccess)
+    e = launch_convert_out(src, 0, s.ldb, ell, s.d, dst, dtype == FD_F64, s.d, valid, b->st);
+  if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(out, tmp, ob, cudaMemcpyDeviceToHost, b->st);
+  if (e == cudaSuccess && tmp) e = cudaStreamSynchronize(b->st);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return batch_fail(e, "batch sketch out");
+  return FD_OK;
+}
+
+extern "C" int fd_batch_sketch_all(fd_batch_state* b, float* out, const int64_t* offsets) {
+  if (!b || !out || !offsets) return FD_EINVAL;
+  cudaError_t e = cudaSuccess;
+  if (!b->doffs) {
+    e = cudaMalloc(&b->doffs, (size_t)b->count * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&b->fctr_all, (size_t)b->count * sizeof(DevCounters));
+    if (e != cudaSuccess) return batch_fail(e, "sketch_all alloc");
+  }
+  e = cudaMemcpyAsync(b->doffs, offsets, (size_t)b->count * sizeof(long long),
+                      cudaMemcpyHostToDevice, b->st);
+  if (e != cudaSuccess) return batch_fail(e, "sketch_all offsets");
+  const double eps = 1.1920928955078125e-07;
+  const int grid = std::min(b->count, 2 * b->nsm);
+  batch_flush_all_kernel<<<grid, BT, BATCH_SMEM, b->st>>>(b->dsk, b->count, out, b->doffs,
+                                                          b->fctr_all, b->variant, b->alpha,
+                                                          b->max_sweeps,
+                                                          4.0 * eps * std::sqrt((double)BMAX_L));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return batch_fail(e, "batch_flush_all_kernel");
+  return FD_OK;
+}
+
+extern "C" int fd_batch_stats(fd_batch_state* b, int32_t id, fd_stats_t* s) {
+  if (!b || id < 0 || id >= b->count || !s) return FD_EINVAL;
+  DevCounters c[2];
+  cudaError_t e = cudaMemcpyAsync(&c[0], b->ctrs + id, sizeof(DevCounters), cudaMemcpyDeviceToHost, b->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&c[1], b->ctr_flush, sizeof(DevCounters), cudaMemcpyDeviceToHost, b->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return batch_fail(e, "batch stats");
+  std::memset(s, 0, sizeof(*s));
+  s->d = b->d[id];
+  s->ell = b->ell[id];
+  s->variant = b->variant;
+  s->alpha = b->alpha;
+  s->prec = b->prec;
+  s->pending = b->m[id];
+  s->n_seen = b->nseen[id];
+  s->reductions = c[0].reductions;
+  s->noconv = c[0].noconv;
+  s->norm_a2 = c[0].norm_a2;
+  s->sum_delta = c[0].sum_delta;
+  s->last_delta = c[0].last_delta;
+  s->removed = c[0].removed;
+  s->max_sweeps = c[0].max_sweeps;
+  // flush totals refer to the latest fd_batch_sketch call
+  s->sketch_sum_delta = c[1].sum_delta;
+  s->sketch_removed = c[1].removed;
+  s->sketch_norm_b2 = c[1].norm_b2;
+  return FD_OK;
+}
+
+extern "C" int fd_batch_reset(fd_batch_state* b) {
+  if (!b) return FD_EINVAL;
+  size_t total = 0;
+  for (int i = 0; i < b->count; ++i) total += (size_t)2 * b->ell[i] * ((b->d[i] + 3) / 4 * 4);
+  cudaError_t e = cudaMemsetAsync(b->arena, 0, total * sizeof(float), b->st);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(b->ctrs, 0, (size_t)b->count * sizeof(DevCounters), b->st);
+  for (auto& s : b->hs) s.m = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->dsk, b->hs.data(), (size_t)b->count * sizeof(BatchSketch),
+                        cudaMemcpyHostToDevice, b->st);
+  if (e != cudaSuccess) return batch_fail(e, "batch reset");
+  std::fill(b->m.begin(), b->m.end(), 0);
+  std::fill(b->nseen.begin(), b->nseen.end(), 0);
+  return FD_OK;
+}
+
+extern "C" int fd_batch_destroy(fd_batch_state* b) {
+  if (!b) return FD_EINVAL;
+  if (b->st) cudaStreamSynchronize(b->st);
+  cudaFree(b->arena);
+  cudaFree(b->ctrs);
+  cudaFree(b->ctr_flush);
+  cudaFree(b->flush_out);
+  cudaFree(b->dsk);
+  cudaFree(b->ditems);
+  cudaFree(b->next);
+  cudaFree(b->doffs);
+  cudaFree(b->fctr_all);
+  delete b;
+  return FD_OK;
+}

@@ -1,0 +1,253 @@
+// Eigensolve building blocks shared by the single-sketch and batched kernels:
+// loading G, and everything after the Jacobi sweeps (eigenvalues, sort, the
+// FP64 ReduceRank rules of Sec. 2.3 / Algorithms 2-3, the rotate matrix and
+// the FP64 counters).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "fd_internal.cuh"
+
+namespace fdk {
+
+__device__ __forceinline__ int rr_index(int pos, int r, int np) {
+  // position 0 is fixed, the others rotate by one place per round
+  return pos == 0 ? 0 : 1 + (pos - 1 + r) % (np - 1);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T> struct Eps;
+template <> struct Eps<float> { static constexpr double v = 1.1920928955078125e-07; };
+template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
+
+constexpr int EIG_THREADS = 512;
+constexpr int EIG_MAX_EPL = 16;  // elements per lane per column: n <= 512
+
+inline size_t eig_scalar_bytes(int np) {
+  return (size_t)np * (4 * sizeof(double) + 2 * sizeof(int)) + 256;
+}
+
+// Load G = sum of the partial slices (fixed order), symmetrised, into Wm
+// (column j = row j of the symmetric G, stride ld, zero padding to np).
+template <typename T>
+__device__ void eig_load(const EigArgs& a, T* Wm, int ld, int n, int np) {
+  const T* parts = reinterpret_cast<const T*>(a.parts);
+  for (int idx = threadIdx.x; idx < np * ld; idx += blockDim.x) {
+    const int i = idx / ld, j = idx - (idx / ld) * ld;
+    T v = T(0);
+    if (i < n && j < n) {
+      T sij = T(0), sji = T(0);
+      for (int p = 0; p < a.nparts; ++p) {
+        sij += parts[(int64_t)p * a.part_stride + (int64_t)i * a.ldp + j];
+        sji += parts[(int64_t)p * a.part_stride + (int64_t)j * a.ldp + i];
+      }
+      v = T(0.5) * (sij + sji);
+    }
+    Wm[(int64_t)i * ld + j] = v;
+  }
+}
+
+// Steps after the Jacobi sweeps: eigenvalues, sort, ReduceRank (FP64),
+// rotate matrix, counters. `sweep` = sweeps run (== max_sweeps if capped).
+template <typename T>
+__device__ void eig_finish(const EigArgs& a, const T* Wm, int ld, int n, int np, int sweep,
+                           int capped, double wscale, double* lam, double* mu, double* mup,
+                           double* scl, int* ord, int* rrank) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = blockDim.x >> 5;
+  __shared__ int s_count;
+  __shared__ double s_dsum, s_dlast;
+  const int s_sweeps = sweep;
+  // lambda_j = ||w_j|| in FP64 (one warp per column).
+  for (int j = warp; j < np; j += nwarps) {
+    double s = 0.0;
+    for (int i = lane; i < np; i += 32) {
+      const double v = (double)Wm[(int64_t)j * ld + i];
+      s = fma(v, v, s);
+    }
+    s = warp_sum(s);
+    if (lane == 0) lam[j] = (j < n) ? sqrt(s) * wscale : -1.0;  // padding column sorts last
+  }
+  __syncthreads();
+
+  // 4. Sort descending, ties by column index.
+  for (int j = tid; j < np; j += blockDim.x) {
+    const double lj = lam[j];
+    int rank = 0;
+    for (int i = 0; i < np; ++i) {
+      const double li = lam[i];
+      rank += (li > lj) || (li == lj && i < j);
+    }
+    ord[rank] = j;
+  }
+  __syncthreads();
+  for (int k = tid; k < np; k += blockDim.x) {
+    const double v = lam[ord[k]];
+    mu[k] = v > 0.0 ? v : 0.0;
+  }
+  if (tid == 0) { s_dsum = 0.0; s_dlast = 0.0; }
+  __syncthreads();
+
+  // 5. ReduceRank in FP64 on the masses mu_k = sigma_k^2 (k = 0..n-1 sorted).
+  const int ell = a.ell;
+  if (a.variant != FD_VAR_SS) {
+    const double delta = (n >= ell) ? mu[ell - 1] : 0.0;
+    int keep = 0;
+    if (a.variant == FD_VAR_PFD) {
+      // Algorithm 2 keeps floor((1-alpha)*ell) values; alpha > 0 shrinks at least one
+      keep = (int)floor((1.0 - a.alpha) * ell + 1e-9);
+      keep = keep < 0 ? 0 : (keep > ell - 1 ? ell - 1 : keep);
+    }
+    for (int k = tid; k < np; k += blockDim.x) {
+      const double m0 = mu[k];
+      double mp = 0.0;
+      if (k < n) {
+        if (a.variant == FD_VAR_FD) mp = fmax(m0 - delta, 0.0);
+        else if (a.variant == FD_VAR_ISVD) mp = (k < ell - 1) ? m0 : 0.0;
+        else mp = (k < keep) ? m0 : ((k < ell) ? fmax(m0 - delta, 0.0) : 0.0);
+      }
+      mup[k] = mp;
+    }
+    if (tid == 0) { s_dsum = delta; s_dlast = delta; }
+  } else if (warp == 0) {
+    // SS (Algorithm 3, repeated): masses at or below the numerical-rank floor
+    // are empty; then merge the second-smallest into the smallest until ell-1
+    // directions remain. Ties: the larger sorted position counts as smaller.
+    const double flo = mu[0] * (double)np * Eps<T>::v;
+    for (int k = lane; k < np; k += 32) mup[k] = (k < n && mu[k] > flo) ? mu[k] : 0.0;
+    __syncwarp();
+    int alive = 0;
+    for (int k = lane; k < np; k += 32) alive += (mup[k] > 0.0);
+    alive = warp_sum(alive);
+    double dsum = 0.0, dlast = 0.0;
+    while (alive > ell - 1) {
+      // per lane: two smallest alive (mass asc, position desc)
+      double m1 = INFINITY, m2 = INFINITY;
+      int i1 = -1, i2 = -1;
+      for (int k = lane; k < np; k += 32) {
+        const double v = mup[k];
+        if (v <= 0.0) continue;
+        const bool lt1 = (v < m1) || (v == m1 && k > i1);
+        if (lt1) { m2 = m1; i2 = i1; m1 = v; i1 = k; }
+        else {
+          const bool lt2 = (v < m2) || (v == m2 && k > i2);
+          if (lt2) { m2 = v; i2 = k; }
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double om1 = __shfl_xor_sync(0xffffffffu, m1, o);
+        const double om2 = __shfl_xor_sync(0xffffffffu, m2, o);
+        const int oi1 = __shfl_xor_sync(0xffffffffu, i1, o);
+        const int oi2 = __shfl_xor_sync(0xffffffffu, i2, o);
+        // merge two sorted pairs (m1,i1),(m2,i2) and (om1,oi1),(om2,oi2)
+        double c[4] = {m1, m2, om1, om2};
+        int ci[4] = {i1, i2, oi1, oi2};
+        double b1 = INFINITY, b2 = INFINITY;
+        int j1 = -1, j2 = -1;
+        for (int t = 0; t < 4; ++t) {
+          const double v = c[t];
+          const int k = ci[t];
+          if (k < 0 || k == j1) continue;
+          const bool lt1 = (v < b1) || (v == b1 && k > j1);
+          if (lt1) { b2 = b1; j2 = j1; b1 = v; j1 = k; }
+          else if (k != j1) {
+            const bool lt2 = (v < b2) || (v == b2 && k > j2);
+            if (lt2) { b2 = v; j2 = k; }
+          }
+        }
+        m1 = b1; i1 = j1; m2 = b2; i2 = j2;
+      }
+      // i1 = q (smallest), i2 = p (second smallest)
+      if (lane == 0) {
+        const double dp = mup[i2];
+        mup[i1] = mup[i1] + dp;
+        mup[i2] = 0.0;
+        dsum += dp;
+        dlast = dp;
+      }
+      __syncwarp();
+      --alive;
+    }
+    if (lane == 0) { s_dsum = dsum; s_dlast = dlast; }
+  }
+  __syncthreads();
+
+  // 6. Output order: retained positions by sigma'^2 descending, ties by position.
+  for (int k = tid; k < np; k += blockDim.x) {
+    const double v = mup[k];
+    int rank = -1;
+    if (v > 0.0) {
+      rank = 0;
+      for (int i = 0; i < np; ++i) {
+        const double w = mup[i];
+        rank += (w > v) || (w == v && i < k);
+      }
+    }
+    rrank[k] = rank;
+    // scale of column w_j: sigma'/sigma / lambda = sqrt(mu'/mu) / mu
+    scl[k] = (v > 0.0 && mu[k] > 0.0) ? sqrt(v / mu[k]) / mu[k] : 0.0;
+  }
+  if (tid == 0) {
+    int cnt = 0;
+    for (int k = 0; k < np; ++k) cnt += (mup[k] > 0.0);
+    s_count = cnt;
+  }
+  __syncthreads();
+
+  // 7. Rotate matrix rows 0..ell-2: row r = scale * w_j (zero rows past the count).
+  const int nout = ell - 1;
+  T* wr = reinterpret_cast<T*>(a.wrot);
+  for (int idx = tid; idx < nout * n; idx += blockDim.x) {
+    const int r = idx / n, i = idx - (idx / n) * n;
+    if (r >= s_count) {
+      wr[(int64_t)r * a.ldr + i] = T(0);
+      if (a.wrot_hi) {
+        a.wrot_hi[(int64_t)r * a.ldr16 + i] = __float2bfloat16_rn(0.0f);
+        a.wrot_lo[(int64_t)r * a.ldr16 + i] = __float2bfloat16_rn(0.0f);
+      }
+    }
+  }
+  for (int k = warp; k < np; k += nwarps) {
+    const int r = rrank[k];
+    if (r < 0 || r >= nout) continue;
+    const int j = ord[k];
+    const double sc = scl[k] * wscale;
+    for (int i = lane; i < n; i += 32) {
+      const double v = sc * (double)Wm[(int64_t)j * ld + i];
+      wr[(int64_t)r * a.ldr + i] = (T)v;
+      if (a.wrot_hi) {
+        const float vf = (float)v;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(vf);
+        a.wrot_hi[(int64_t)r * a.ldr16 + i] = hi;
+        a.wrot_lo[(int64_t)r * a.ldr16 + i] = __float2bfloat16_rn(vf - __bfloat162float(hi));
+      }
+    }
+  }
+
+  // 8. FP64 bookkeeping and diagnostics.
+  if (a.sig2_out) for (int k = tid; k < n; k += blockDim.x) { a.sig2_out[k] = mu[k]; a.sigp2_out[k] = mup[k]; }
+  if (tid == 0) {
+    DevCounters c = *a.ctr_in;
+    double rem = 0.0, nb = 0.0;
+    for (int k = 0; k < n; ++k) { rem += mu[k] - mup[k]; nb += mup[k]; }
+    c.sum_delta += s_dsum;
+    c.last_delta = s_dlast;
+    c.removed += rem;
+    c.norm_b2 = nb;
+    c.reductions += 1;
+    c.noconv += capped ? 1 : 0;
+    c.max_sweeps = fmax(c.max_sweeps, (double)s_sweeps);
+    c.retained = s_count < nout ? s_count : nout;
+    *a.ctr_out = c;
+  }
+}
+
+
+}  // namespace fdk

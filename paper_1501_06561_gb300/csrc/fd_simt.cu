@@ -12,6 +12,8 @@
 #include <cstdio>
 
 #include "fd_internal.cuh"
+#include "fd_jacobi.cuh"
+#include "fd_eig.cuh"
 
 namespace fdk {
 
@@ -182,244 +184,6 @@ int gram_simt_slices(int64_t d, int ksplit) {
 // Eigenvalues lambda_j = ||w_j|| are formed in FP64 and the ReduceRank rule
 // of the variant runs in FP64 (Sec. 2.3, Algorithms 2 and 3).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int rr_index(int pos, int r, int np) {
-  // position 0 is fixed, the others rotate by one place per round
-  return pos == 0 ? 0 : 1 + (pos - 1 + r) % (np - 1);
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-template <typename T> struct Eps;
-template <> struct Eps<float> { static constexpr double v = 1.1920928955078125e-07; };
-template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
-
-constexpr int EIG_THREADS = 512;
-constexpr int EIG_MAX_EPL = 16;  // elements per lane per column: n <= 512
-
-size_t eig_scalar_bytes(int np) {
-  return (size_t)np * (4 * sizeof(double) + 2 * sizeof(int)) + 256;
-}
-
-// Load G = sum of the partial slices (fixed order), symmetrised, into Wm
-// (column j = row j of the symmetric G, stride ld, zero padding to np).
-template <typename T>
-__device__ void eig_load(const EigArgs& a, T* Wm, int ld, int n, int np) {
-  const T* parts = reinterpret_cast<const T*>(a.parts);
-  for (int idx = threadIdx.x; idx < np * ld; idx += blockDim.x) {
-    const int i = idx / ld, j = idx - (idx / ld) * ld;
-    T v = T(0);
-    if (i < n && j < n) {
-      T sij = T(0), sji = T(0);
-      for (int p = 0; p < a.nparts; ++p) {
-        sij += parts[(int64_t)p * a.part_stride + (int64_t)i * a.ldp + j];
-        sji += parts[(int64_t)p * a.part_stride + (int64_t)j * a.ldp + i];
-      }
-      v = T(0.5) * (sij + sji);
-    }
-    Wm[(int64_t)i * ld + j] = v;
-  }
-}
-
-// Steps after the Jacobi sweeps: eigenvalues, sort, ReduceRank (FP64),
-// rotate matrix, counters. `sweep` = sweeps run (== max_sweeps if capped).
-template <typename T>
-__device__ void eig_finish(const EigArgs& a, const T* Wm, int ld, int n, int np, int sweep,
-                           int capped, double* lam, double* mu, double* mup, double* scl,
-                           int* ord, int* rrank) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nwarps = blockDim.x >> 5;
-  __shared__ int s_count;
-  __shared__ double s_dsum, s_dlast;
-  const int s_sweeps = sweep;
-  // lambda_j = ||w_j|| in FP64 (one warp per column).
-  for (int j = warp; j < np; j += nwarps) {
-    double s = 0.0;
-    for (int i = lane; i < np; i += 32) {
-      const double v = (double)Wm[(int64_t)j * ld + i];
-      s = fma(v, v, s);
-    }
-    s = warp_sum(s);
-    if (lane == 0) lam[j] = (j < n) ? sqrt(s) : -1.0;  // padding column sorts last
-  }
-  __syncthreads();
-
-  // 4. Sort descending, ties by column index.
-  for (int j = tid; j < np; j += blockDim.x) {
-    const double lj = lam[j];
-    int rank = 0;
-    for (int i = 0; i < np; ++i) {
-      const double li = lam[i];
-      rank += (li > lj) || (li == lj && i < j);
-    }
-    ord[rank] = j;
-  }
-  __syncthreads();
-  for (int k = tid; k < np; k += blockDim.x) {
-    const double v = lam[ord[k]];
-    mu[k] = v > 0.0 ? v : 0.0;
-  }
-  if (tid == 0) { s_dsum = 0.0; s_dlast = 0.0; }
-  __syncthreads();
-
-  // 5. ReduceRank in FP64 on the masses mu_k = sigma_k^2 (k = 0..n-1 sorted).
-  const int ell = a.ell;
-  if (a.variant != FD_VAR_SS) {
-    const double delta = (n >= ell) ? mu[ell - 1] : 0.0;
-    int keep = 0;
-    if (a.variant == FD_VAR_PFD) {
-      // Algorithm 2 keeps floor((1-alpha)*ell) values; alpha > 0 shrinks at least one
-      keep = (int)floor((1.0 - a.alpha) * ell + 1e-9);
-      keep = keep < 0 ? 0 : (keep > ell - 1 ? ell - 1 : keep);
-    }
-    for (int k = tid; k < np; k += blockDim.x) {
-      const double m0 = mu[k];
-      double mp = 0.0;
-      if (k < n) {
-        if (a.variant == FD_VAR_FD) mp = fmax(m0 - delta, 0.0);
-        else if (a.variant == FD_VAR_ISVD) mp = (k < ell - 1) ? m0 : 0.0;
-        else mp = (k < keep) ? m0 : ((k < ell) ? fmax(m0 - delta, 0.0) : 0.0);
-      }
-      mup[k] = mp;
-    }
-    if (tid == 0) { s_dsum = delta; s_dlast = delta; }
-  } else if (warp == 0) {
-    // SS (Algorithm 3, repeated): masses at or below the numerical-rank floor
-    // are empty; then merge the second-smallest into the smallest until ell-1
-    // directions remain. Ties: the larger sorted position counts as smaller.
-    const double flo = mu[0] * (double)np * Eps<T>::v;
-    for (int k = lane; k < np; k += 32) mup[k] = (k < n && mu[k] > flo) ? mu[k] : 0.0;
-    __syncwarp();
-    int alive = 0;
-    for (int k = lane; k < np; k += 32) alive += (mup[k] > 0.0);
-    alive = warp_sum(alive);
-    double dsum = 0.0, dlast = 0.0;
-    while (alive > ell - 1) {
-      // per lane: two smallest alive (mass asc, position desc)
-      double m1 = INFINITY, m2 = INFINITY;
-      int i1 = -1, i2 = -1;
-      for (int k = lane; k < np; k += 32) {
-        const double v = mup[k];
-        if (v <= 0.0) continue;
-        const bool lt1 = (v < m1) || (v == m1 && k > i1);
-        if (lt1) { m2 = m1; i2 = i1; m1 = v; i1 = k; }
-        else {
-          const bool lt2 = (v < m2) || (v == m2 && k > i2);
-          if (lt2) { m2 = v; i2 = k; }
-        }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double om1 = __shfl_xor_sync(0xffffffffu, m1, o);
-        const double om2 = __shfl_xor_sync(0xffffffffu, m2, o);
-        const int oi1 = __shfl_xor_sync(0xffffffffu, i1, o);
-        const int oi2 = __shfl_xor_sync(0xffffffffu, i2, o);
-        // merge two sorted pairs (m1,i1),(m2,i2) and (om1,oi1),(om2,oi2)
-        double c[4] = {m1, m2, om1, om2};
-        int ci[4] = {i1, i2, oi1, oi2};
-        double b1 = INFINITY, b2 = INFINITY;
-        int j1 = -1, j2 = -1;
-        for (int t = 0; t < 4; ++t) {
-          const double v = c[t];
-          const int k = ci[t];
-          if (k < 0 || k == j1) continue;
-          const bool lt1 = (v < b1) || (v == b1 && k > j1);
-          if (lt1) { b2 = b1; j2 = j1; b1 = v; j1 = k; }
-          else if (k != j1) {
-            const bool lt2 = (v < b2) || (v == b2 && k > j2);
-            if (lt2) { b2 = v; j2 = k; }
-          }
-        }
-        m1 = b1; i1 = j1; m2 = b2; i2 = j2;
-      }
-      // i1 = q (smallest), i2 = p (second smallest)
-      if (lane == 0) {
-        const double dp = mup[i2];
-        mup[i1] = mup[i1] + dp;
-        mup[i2] = 0.0;
-        dsum += dp;
-        dlast = dp;
-      }
-      __syncwarp();
-      --alive;
-    }
-    if (lane == 0) { s_dsum = dsum; s_dlast = dlast; }
-  }
-  __syncthreads();
-
-  // 6. Output order: retained positions by sigma'^2 descending, ties by position.
-  for (int k = tid; k < np; k += blockDim.x) {
-    const double v = mup[k];
-    int rank = -1;
-    if (v > 0.0) {
-      rank = 0;
-      for (int i = 0; i < np; ++i) {
-        const double w = mup[i];
-        rank += (w > v) || (w == v && i < k);
-      }
-    }
-    rrank[k] = rank;
-    // scale of column w_j: sigma'/sigma / lambda = sqrt(mu'/mu) / mu
-    scl[k] = (v > 0.0 && mu[k] > 0.0) ? sqrt(v / mu[k]) / mu[k] : 0.0;
-  }
-  if (tid == 0) {
-    int cnt = 0;
-    for (int k = 0; k < np; ++k) cnt += (mup[k] > 0.0);
-    s_count = cnt;
-  }
-  __syncthreads();
-
-  // 7. Rotate matrix rows 0..ell-2: row r = scale * w_j (zero rows past the count).
-  const int nout = ell - 1;
-  T* wr = reinterpret_cast<T*>(a.wrot);
-  for (int idx = tid; idx < nout * n; idx += blockDim.x) {
-    const int r = idx / n, i = idx - (idx / n) * n;
-    if (r >= s_count) {
-      wr[(int64_t)r * a.ldr + i] = T(0);
-      if (a.wrot_hi) {
-        a.wrot_hi[(int64_t)r * a.ldr16 + i] = __float2bfloat16_rn(0.0f);
-        a.wrot_lo[(int64_t)r * a.ldr16 + i] = __float2bfloat16_rn(0.0f);
-      }
-    }
-  }
-  for (int k = warp; k < np; k += nwarps) {
-    const int r = rrank[k];
-    if (r < 0 || r >= nout) continue;
-    const int j = ord[k];
-    const double sc = scl[k];
-    for (int i = lane; i < n; i += 32) {
-      const double v = sc * (double)Wm[(int64_t)j * ld + i];
-      wr[(int64_t)r * a.ldr + i] = (T)v;
-      if (a.wrot_hi) {
-        const float vf = (float)v;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(vf);
-        a.wrot_hi[(int64_t)r * a.ldr16 + i] = hi;
-        a.wrot_lo[(int64_t)r * a.ldr16 + i] = __float2bfloat16_rn(vf - __bfloat162float(hi));
-      }
-    }
-  }
-
-  // 8. FP64 bookkeeping and diagnostics.
-  if (a.sig2_out) for (int k = tid; k < n; k += blockDim.x) { a.sig2_out[k] = mu[k]; a.sigp2_out[k] = mup[k]; }
-  if (tid == 0) {
-    DevCounters c = *a.ctr_in;
-    double rem = 0.0, nb = 0.0;
-    for (int k = 0; k < n; ++k) { rem += mu[k] - mup[k]; nb += mup[k]; }
-    c.sum_delta += s_dsum;
-    c.last_delta = s_dlast;
-    c.removed += rem;
-    c.norm_b2 = nb;
-    c.reductions += 1;
-    c.noconv += capped ? 1 : 0;
-    c.max_sweeps = fmax(c.max_sweeps, (double)s_sweeps);
-    c.retained = s_count < nout ? s_count : nout;
-    *a.ctr_out = c;
-  }
-}
-
 template <typename T>
 __global__ void __launch_bounds__(EIG_THREADS) eig_shrink_kernel(EigArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -502,16 +266,14 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_shrink_kernel(EigArgs a) {
   // sweeps run: the last one found no pair to rotate, unless the cap was hit
   const int sweeps_run = (sweep < a.max_sweeps) ? sweep + 1 : a.max_sweeps;
 
-  eig_finish<T>(a, Wm, ld, n, np, sweeps_run, sweep >= a.max_sweeps, lam, mu, mup, scl, ord,
-                rrank);
+  eig_finish<T>(a, Wm, ld, n, np, sweeps_run, sweep >= a.max_sweeps, 1.0, lam, mu, mup, scl,
+                ord, rrank);
 }
 
-// FP32 Jacobi with GS lanes per column pair, float4 column access, column
-// norms carried through the sweep by the exact update
-//   ||w_p'||^2 = ||w_p||^2 - t*gamma,  ||w_q'||^2 = ||w_q||^2 + t*gamma
-// (recomputed from the data at every sweep start, and at once when the update
-// cancels more than three quarters of a norm).
-template <int GS, int MAXV, int NT>
+// FP32 eigensolve with G in shared memory (one-sided Jacobi of fd_jacobi.cuh),
+// G scaled by its largest diagonal entry so that every column norm is at most
+// np whatever the scale of the rows.
+template <int GS, int MAXV, int MAXP, int NT>
 __global__ void __launch_bounds__(NT) eig_fast_kernel(EigArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = a.n;
@@ -528,94 +290,25 @@ __global__ void __launch_bounds__(NT) eig_fast_kernel(EigArgs a) {
   double* scl = mup + np;
   int* ord = reinterpret_cast<int*>(scl + np);
   int* rrank = ord + np;
+  __shared__ float s_max;
 
   eig_load<float>(a, Wm, ld, n, np);
+  if (tid == 0) s_max = 0.f;
   __syncthreads();
-
-  const int g = tid / GS, gl = tid % GS;
-  const int ngroups = NT / GS;
-  const unsigned gmask = (GS == 32) ? 0xffffffffu
-                                    : (((1u << GS) - 1u) << ((tid & 31) & ~(GS - 1)));
-  const int nv = (np + 3) >> 2;  // float4 chunks per column
-  const int npairs = np / 2, nrounds = np - 1;
-  const float tol = (float)a.tol;
-
-  auto col_sq = [&](const float* w) {
-    float s = 0.f;
-#pragma unroll
-    for (int c = 0; c < MAXV; ++c) {
-      const int v = c * GS + gl;
-      if (v < nv) {
-        const float4 x = reinterpret_cast<const float4*>(w)[v];
-        s = fmaf(x.x, x.x, s); s = fmaf(x.y, x.y, s); s = fmaf(x.z, x.z, s); s = fmaf(x.w, x.w, s);
-      }
-    }
-#pragma unroll
-    for (int o = GS / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, GS);
-    return s;
-  };
-
-  int sweep = 0;
-  for (; sweep < a.max_sweeps; ++sweep) {
-    // exact norms at the start of the sweep
-    for (int j = g; j < np; j += ngroups) {
-      const float s = col_sq(Wm + (int64_t)j * ld);
-      if (gl == 0) nrm[j] = s;
-    }
-    __syncthreads();
-    int rotated = 0;
-    for (int r = 0; r < nrounds; ++r) {
-      for (int k = g; k < npairs; k += ngroups) {
-        const int p = rr_index(k, r, np);
-        const int q = rr_index(np - 1 - k, r, np);
-        float4* wp = reinterpret_cast<float4*>(Wm + (int64_t)p * ld);
-        float4* wq = reinterpret_cast<float4*>(Wm + (int64_t)q * ld);
-        float4 xp[MAXV], xq[MAXV];
-        float ga = 0.f;
-#pragma unroll
-        for (int c = 0; c < MAXV; ++c) {
-          const int v = c * GS + gl;
-          if (v < nv) { xp[c] = wp[v]; xq[c] = wq[v]; }
-          else { xp[c] = make_float4(0.f, 0.f, 0.f, 0.f); xq[c] = xp[c]; }
-          ga = fmaf(xp[c].x, xq[c].x, ga); ga = fmaf(xp[c].y, xq[c].y, ga);
-          ga = fmaf(xp[c].z, xq[c].z, ga); ga = fmaf(xp[c].w, xq[c].w, ga);
-        }
-#pragma unroll
-        for (int o = GS / 2; o > 0; o >>= 1) ga += __shfl_xor_sync(gmask, ga, o, GS);
-        const float al = nrm[p], be = nrm[q];
-        if (ga != 0.f && fabsf(ga) > tol * sqrtf(al * be)) {
-          const float zeta = (be - al) / (2.f * ga);
-          const float az = fabsf(zeta);
-          const float t = (az > 1e15f) ? 0.5f / zeta : copysignf(1.f, zeta) / (az + sqrtf(1.f + zeta * zeta));
-          const float cs = rsqrtf(1.f + t * t);
-          const float sn = cs * t;
-#pragma unroll
-          for (int c = 0; c < MAXV; ++c) {
-            const int v = c * GS + gl;
-            if (v < nv) {
-              float4 a4, b4;
-              a4.x = cs * xp[c].x - sn * xq[c].x; b4.x = sn * xp[c].x + cs * xq[c].x;
-              a4.y = cs * xp[c].y - sn * xq[c].y; b4.y = sn * xp[c].y + cs * xq[c].y;
-              a4.z = cs * xp[c].z - sn * xq[c].z; b4.z = sn * xp[c].z + cs * xq[c].z;
-              a4.w = cs * xp[c].w - sn * xq[c].w; b4.w = sn * xp[c].w + cs * xq[c].w;
-              wp[v] = a4;
-              wq[v] = b4;
-            }
-          }
-          float na = al - t * ga, nb = be + t * ga;
-          if (na < 0.25f * al) na = col_sq(reinterpret_cast<float*>(wp));
-          if (nb < 0.25f * be) nb = col_sq(reinterpret_cast<float*>(wq));
-          if (gl == 0) { nrm[p] = na; nrm[q] = nb; }
-          rotated = 1;
-        }
-      }
-      __syncthreads();
-    }
-    if (!__syncthreads_or(rotated)) break;
-  }
-  const int sweeps_run = (sweep < a.max_sweeps) ? sweep + 1 : a.max_sweeps;
-  eig_finish<float>(a, Wm, ld, n, np, sweeps_run, sweep >= a.max_sweeps, lam, mu, mup, scl, ord,
-                    rrank);
+  float dm = 0.f;
+  for (int i = tid; i < n; i += blockDim.x) dm = fmaxf(dm, fabsf(Wm[(size_t)i * ld + i]));
+  for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+  if ((tid & 31) == 0) atomicMax(reinterpret_cast<int*>(&s_max), __float_as_int(dm));
+  __syncthreads();
+  const float smax = s_max;
+  const float inv = (smax > 0.f) ? 1.f / smax : 1.f;
+  for (int idx = tid; idx < np * ld; idx += blockDim.x) Wm[idx] *= inv;
+  __syncthreads();
+  int capped = 0;
+  const int sweeps = jacobi_sweeps_f32<GS, MAXV, MAXP>(Wm, ld, np, nrm, a.max_sweeps,
+                                                        (float)a.tol, &capped);
+  eig_finish<float>(a, Wm, ld, n, np, sweeps, capped, (smax > 0.f) ? (double)smax : 1.0, lam,
+                    mu, mup, scl, ord, rrank);
 }
 
 size_t eig_fast_smem(int np) {
@@ -624,12 +317,20 @@ size_t eig_fast_smem(int np) {
          eig_scalar_bytes(np);
 }
 
-template <int GS, int MAXV, int NT>
+template <int GS, int MAXV, int MAXP, int NT>
 cudaError_t launch_fast(const EigArgs& a, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(eig_fast_kernel<GS, MAXV, NT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  eig_fast_kernel<GS, MAXV, NT><<<1, NT, smem, st>>>(a);
+  static size_t attr_set = 0;  // largest dynamic size granted so far for this instantiation
+  if (smem > attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(eig_fast_kernel<GS, MAXV, MAXP, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = smem;
+  }
+  const int np = a.n + (a.n & 1);
+  int threads = ((np / 2) * GS + 31) / 32 * 32;
+  if (threads > NT) threads = NT;
+  if (threads < 64) threads = 64;
+  eig_fast_kernel<GS, MAXV, MAXP, NT><<<1, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -638,11 +339,11 @@ cudaError_t launch_fast(const EigArgs& a, size_t smem, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_eig_shrink(const EigArgs& a, cudaStream_t st) {
   const int np = a.n + (a.n & 1);
-  if (sizeof(T) == 4 && a.work == nullptr && np <= 224 && eig_fast_smem(np) <= 227 * 1024) {
+  if (sizeof(T) == 4 && a.work == nullptr && np <= 224 && eig_fast_smem(np) <= 226 * 1024) {
     const size_t smem = eig_fast_smem(np);
-    if (np <= 64) return launch_fast<8, 2, 256>(a, smem, st);
-    if (np <= 128) return launch_fast<8, 4, 512>(a, smem, st);
-    return launch_fast<16, 4, 1024>(a, smem, st);
+    if (np <= 64) return launch_fast<8, 2, 1, 256>(a, smem, st);
+    if (np <= 128) return launch_fast<8, 4, 1, 512>(a, smem, st);
+    return launch_fast<16, 4, 2, 1024>(a, smem, st);
   }
   size_t smem = eig_scalar_bytes(np);
   if (a.work == nullptr) smem += (((size_t)np * np * sizeof(T) + 15) & ~(size_t)15);
@@ -659,9 +360,9 @@ template cudaError_t launch_eig_shrink<double>(const EigArgs&, cudaStream_t);
 // Whether the eigensolve of an n-row reduction keeps G in shared memory.
 bool eig_fits_smem(int n, size_t elem) {
   const int np = n + (n & 1);
-  if (elem == 4 && np <= 224 && eig_fast_smem(np) <= 227 * 1024) return true;
+  if (elem == 4 && np <= 224 && eig_fast_smem(np) <= 226 * 1024) return true;
   const size_t need = eig_scalar_bytes(np) + (((size_t)np * np * elem + 15) & ~(size_t)15);
-  return need <= 227 * 1024;
+  return need <= 226 * 1024;
 }
 
 // ---------------------------------------------------------------------------

@@ -542,8 +542,9 @@ int tc_ingest(TcCtx* t, const void* src, int64_t n, int64_t ld, int dtype, int r
   return FD_OK;
 }
 
-int tc_reduce(TcCtx* t, int nrows, const EigArgs& tmpl, int write_sketch, float* sketch_out,
-              int64_t ldo) {
+// One reduction in three launches (Gram, eigensolve + shrink, rotate), split
+// so that the caller can time each.
+int tc_gram(TcCtx* t, int nrows) {
   cudaError_t e;
   if (nrows < t->L) {
     // a flush of fewer rows: rows nrows..L-1 hold earlier input, free slots
@@ -576,7 +577,11 @@ int tc_reduce(TcCtx* t, int nrows, const EigArgs& tmpl, int write_sketch, float*
   e = cudaLaunchKernelEx(&cfg, gram_tc_kernel, t->m_rm_hi, t->m_rm_lo2, t->G, t->L, nrows, kblocks,
                          t->ks, side, t->err);
   if (e != cudaSuccess) { set_cuda_error(e, "gram_tc_kernel"); return FD_ECUDA; }
-  // eigensolve + shrink, writing the split rotate matrix
+  return FD_OK;
+}
+
+int tc_eig(TcCtx* t, const EigArgs& tmpl) {
+  cudaError_t e;
   EigArgs a = tmpl;
   a.parts = t->G;
   a.nparts = 1;
@@ -590,7 +595,11 @@ int tc_reduce(TcCtx* t, int nrows, const EigArgs& tmpl, int write_sketch, float*
   a.ldr16 = t->ldl;
   e = launch_eig_shrink_f32(a, t->st);
   if (e != cudaSuccess) { set_cuda_error(e, "eig_shrink (tc)"); return FD_ECUDA; }
-  // rotate
+  return FD_OK;
+}
+
+int tc_rotate(TcCtx* t, int nrows, int write_sketch, float* sketch_out, int64_t ldo) {
+  cudaError_t e;
   const int kb_rot = (nrows + 63) / 64;
   const unsigned grid = (unsigned)((t->d + 127) / 128);
   rotate_tc_kernel<<<grid, TC_THREADS, t->rot_smem, t->st>>>(
@@ -599,6 +608,19 @@ int tc_reduce(TcCtx* t, int nrows, const EigArgs& tmpl, int write_sketch, float*
       t->err);
   e = cudaGetLastError();
   if (e != cudaSuccess) { set_cuda_error(e, "rotate_tc_kernel"); return FD_ECUDA; }
+  return FD_OK;
+}
+
+// Zero the buffer planes (a fresh, empty sketch).
+int tc_reset(TcCtx* t) {
+  const size_t plane_rm = (size_t)t->L * t->ldb * 2;
+  const size_t plane_cm = (size_t)t->ldb * t->ldl * 2;
+  cudaError_t e = cudaMemsetAsync(t->rm_hi, 0, plane_rm, t->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->rm_lo2, 0, plane_rm, t->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->cm_hi, 0, plane_cm, t->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->cm_lo, 0, plane_cm, t->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->err, 0, sizeof(int), t->st);
+  if (e != cudaSuccess) { set_cuda_error(e, "tc_reset"); return FD_ECUDA; }
   return FD_OK;
 }
 

@@ -44,6 +44,11 @@ class Stats(ctypes.Structure):
                 ("sketch_norm_b2", ctypes.c_double)]
 
 
+class Work(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int32), ("dtype", ctypes.c_int32), ("rows", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("ld", ctypes.c_int64)]
+
+
 def load():
     """Load libfdsketch.so (raises if it is missing: there is no fallback)."""
     global _lib
@@ -64,7 +69,18 @@ def load():
         "fd_stats": [vp, ctypes.POINTER(Stats)],
         "fd_last_spectrum": [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
         "fd_destroy": [vp],
+        "fd_reset": [vp],
+        "fd_profile": [vp, i32],
+        "fd_kernel_times": [vp, ctypes.POINTER(i64), ctypes.POINTER(dbl)],
         "fd_strerror": [i32],
+        "fd_batch_create": [i32, ctypes.POINTER(i64), ctypes.POINTER(i32), i32, dbl, i32, vp,
+                            ctypes.POINTER(vp)],
+        "fd_batch_append": [vp, ctypes.POINTER(Work), i32],
+        "fd_batch_sketch": [vp, i32, vp, i32, i32],
+        "fd_batch_stats": [vp, i32, ctypes.POINTER(Stats)],
+        "fd_batch_sketch_all": [vp, vp, ctypes.POINTER(i64)],
+        "fd_batch_reset": [vp],
+        "fd_batch_destroy": [vp],
         "fd_version": [],
     }
     for name, args in sig.items():
@@ -176,6 +192,20 @@ class FDSketch:
                "fd_last_spectrum")
         return a, b
 
+    def reset(self):
+        _check(load().fd_reset(self._h), "fd_reset")
+
+    def profile(self, enable: bool = True):
+        _check(load().fd_profile(self._h, 1 if enable else 0), "fd_profile")
+
+    def kernel_times(self):
+        """{class: (launches, device ms)} since profiling was enabled."""
+        c = (ctypes.c_int64 * 4)()
+        m = (ctypes.c_double * 4)()
+        _check(load().fd_kernel_times(self._h, c, m), "fd_kernel_times")
+        names = ("ingest", "gram", "eig", "rotate")
+        return {names[i]: (int(c[i]), float(m[i])) for i in range(4)}
+
     def close(self):
         if getattr(self, "_h", None):
             load().fd_destroy(self._h)
@@ -209,3 +239,103 @@ def cov_err_pair(A, B, stream=None):
                                ctypes.byref(c), ctypes.byref(lo), ctypes.byref(hi)),
            "fd_cov_err_pair")
     return c.value, lo.value, hi.value
+
+
+class FDBatch:
+    """Many independent sketches updated together (fd_batch_* calls)."""
+
+    def __init__(self, ds, ells, variant: str = "fd", alpha: float = 1.0, prec: str = "fp32",
+                 stream=None):
+        lib = load()
+        self.ds = [int(x) for x in ds]
+        self.ells = [int(x) for x in ells]
+        n = len(self.ds)
+        d_arr = (ctypes.c_int64 * n)(*self.ds)
+        e_arr = (ctypes.c_int32 * n)(*self.ells)
+        h = ctypes.c_void_p()
+        _check(lib.fd_batch_create(n, d_arr, e_arr, VARIANT[variant], float(alpha), PREC[prec],
+                                   _stream_ptr(stream), ctypes.byref(h)), "fd_batch_create")
+        self._h = h
+        self._keep = []
+
+    def append(self, blocks):
+        """blocks: {sketch id: CUDA tensor of rows} (one block per sketch per call)."""
+        blocks = {k: v for k, v in blocks.items() if v.shape[0] > 0}
+        if not blocks:
+            return []
+        items = (Work * len(blocks))()
+        keep = []
+        for i, (sid, x) in enumerate(blocks.items()):
+            ptr, n, ld, code, dev, k = _as_rows(x)
+            if not dev:
+                raise ValueError("batched rows must be CUDA tensors")
+            items[i] = Work(int(sid), code, ptr, n, ld)
+            keep.append(k)
+        _check(load().fd_batch_append(self._h, items, len(blocks)), "fd_batch_append")
+        self._keep = keep   # rows must stay alive until the stream passes the call
+        return keep
+
+    def sketch(self, sid: int, dtype=np.float64):
+        B = np.empty((self.ells[sid], self.ds[sid]), dtype=dtype)
+        code = F64 if B.dtype == np.float64 else F32
+        _check(load().fd_batch_sketch(self._h, sid, ctypes.c_void_p(B.ctypes.data), code, 0),
+               "fd_batch_sketch")
+        return B
+
+    def offsets(self):
+        """Element offsets of every sketch in a sketch_all buffer, and its size."""
+        offs, tot = [], 0
+        for d, e in zip(self.ds, self.ells):
+            offs.append(tot)
+            tot += d * e
+        return offs, tot
+
+    def sketch_all(self, out):
+        """All sketches into the CUDA float32 tensor `out` (size from offsets())."""
+        offs, tot = self.offsets()
+        if out.numel() < tot:
+            raise ValueError("output buffer too small")
+        arr = (ctypes.c_int64 * len(offs))(*offs)
+        _check(load().fd_batch_sketch_all(self._h, ctypes.c_void_p(out.data_ptr()), arr),
+               "fd_batch_sketch_all")
+        return out
+
+    def prepare(self, blocks):
+        """Build the work-item array once for repeated appends of the same rows."""
+        blocks = {k: v for k, v in blocks.items() if v.shape[0] > 0}
+        items = (Work * len(blocks))()
+        keep = []
+        for i, (sid, x) in enumerate(blocks.items()):
+            ptr, n, ld, code, dev, k = _as_rows(x)
+            items[i] = Work(int(sid), code, ptr, n, ld)
+            keep.append(k)
+        return items, len(blocks), keep
+
+    def append_prepared(self, prep):
+        items, n, _ = prep
+        _check(load().fd_batch_append(self._h, items, n), "fd_batch_append")
+
+    def stats(self, sid: int) -> dict:
+        s = Stats()
+        _check(load().fd_batch_stats(self._h, sid, ctypes.byref(s)), "fd_batch_stats")
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def reset(self):
+        _check(load().fd_batch_reset(self._h), "fd_batch_reset")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fd_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -153,3 +153,48 @@ def low_rank_rows(n: int, d: int, rank: int, seed: int = 6, dtype=np.float64) ->
     """Rows spanning exactly ``rank`` dimensions (for exact-recovery checks)."""
     rng = _rng(seed, 17)
     return (rng.standard_normal((n, rank)) @ rng.standard_normal((rank, d))).astype(dtype)
+
+
+def random_noisy_device(n: int, d: int, m: int, seed: int, zeta: float = 10.0,
+                        device="cuda", dtype=None, out=None):
+    """Random Noisy rows generated on a CUDA device with PyTorch's generator
+    (for streams too large to draw on the host); same recipe as
+    ``random_noisy``: A = S D U + F / zeta, D from 1 to 0.1, U orthonormal
+    rows. Rounded to ``dtype`` (default bfloat16). Returns an (n, d) tensor."""
+    import torch
+    dtype = torch.bfloat16 if dtype is None else dtype
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    q, r = torch.linalg.qr(torch.randn(d, m, generator=g, device=device, dtype=torch.float32))
+    q = q * torch.sign(torch.diagonal(r))[None, :]
+    Dg = torch.linspace(1.0, 0.1, m, device=device) if m > 1 else torch.ones(1, device=device)
+    DU = Dg[:, None] * q.T
+    if out is None:
+        out = torch.empty(n, d, device=device, dtype=dtype)
+    step = 1 << 14
+    for r0 in range(0, n, step):
+        r1 = min(n, r0 + step)
+        S = torch.randn(r1 - r0, m, generator=g, device=device, dtype=torch.float32)
+        F = torch.randn(r1 - r0, d, generator=g, device=device, dtype=torch.float32)
+        out[r0:r1] = (S @ DU + F / zeta).to(dtype)
+    return out
+
+
+def batch_streams_device(specs, device="cuda", dtype=None):
+    """All streams of a batch in one device buffer: returns (flat tensor,
+    list of (offset_elements, n, d)). Stream i follows ``random_noisy_device``
+    with m = ell_i // 2 (at least 1) and seed specs[i]["seed"]."""
+    import torch
+    dtype = torch.bfloat16 if dtype is None else dtype
+    sizes = [sp["n"] * sp["d"] for sp in specs]
+    total = int(sum(sizes))
+    flat = torch.empty(total, device=device, dtype=dtype)
+    views = []
+    off = 0
+    for sp, sz in zip(specs, sizes):
+        v = flat[off:off + sz].view(sp["n"], sp["d"])
+        random_noisy_device(sp["n"], sp["d"], max(1, sp["ell"] // 2), sp["seed"], device=device,
+                            dtype=dtype, out=v)
+        views.append((off, sp["n"], sp["d"]))
+        off += sz
+    return flat, views

@@ -1,0 +1,92 @@
+"""Batched persistent update (fd_batch_*) against the FP64 oracle and against
+single-handle runs, through the C ABI."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import cov_err, fd_sketch
+from paper_1501_06561_gb300 import fd
+from paper_1501_06561_gb300 import workloads as W
+from helpers import COV_ABS, assert_sigma_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    fd.load()
+
+
+def _specs(k, seed):
+    rng = np.random.default_rng(seed)
+    ds = rng.integers(40, 400, size=k)
+    ells = rng.integers(2, 65, size=k)
+    ns = rng.integers(1, 2500, size=k)
+    return [(int(d), int(e), int(n)) for d, e, n in zip(ds, ells, ns)]
+
+
+@pytest.mark.parametrize("variant", ["fd", "pfd", "isvd", "ss"])
+def test_batch_matches_oracle(variant):
+    alpha = 0.2 if variant == "pfd" else 1.0
+    specs = _specs(24, 7)
+    if variant == "ss":   # SS parity on short streams (discrete merge choices)
+        specs = [(d, e, min(n, 2 * e + 2 * (e + 1) + 3)) for d, e, n in specs]
+    data = [W.random_noisy(n, d, m=max(1, e // 2), seed=100 + i, dtype="bf16")
+            for i, (d, e, n) in enumerate(specs)]
+    with fd.FDBatch([s[0] for s in specs], [s[1] for s in specs], variant, alpha) as b:
+        blocks = {i: torch.from_numpy(a).cuda().to(torch.bfloat16) for i, a in enumerate(data)}
+        b.append(blocks)
+        for i, (d, e, n) in enumerate(specs):
+            B = b.sketch(i)
+            Bo, io = fd_sketch(data[i], e, variant, alpha)
+            assert_sigma_parity(B, Bo, io["normA2"], "fp32", what=f"batch {i} {specs[i]}")
+            assert abs(cov_err(data[i], B) - cov_err(data[i], Bo)) <= COV_ABS
+            st = b.stats(i)
+            assert abs(st["norm_a2"] - io["normA2"]) <= 1e-12 * io["normA2"]
+            assert st["n_seen"] == n
+
+
+def test_batch_split_appends_bit_identical():
+    specs = _specs(10, 9)
+    data = [torch.from_numpy(W.random_noisy(n, d, m=3, seed=i, dtype=np.float32)).cuda()
+            for i, (d, e, n) in enumerate(specs)]
+    with fd.FDBatch([s[0] for s in specs], [s[1] for s in specs]) as b1, \
+            fd.FDBatch([s[0] for s in specs], [s[1] for s in specs]) as b2:
+        b1.append({i: x for i, x in enumerate(data)})
+        half = {i: x[: x.shape[0] // 3] for i, x in enumerate(data)}
+        rest = {i: x[x.shape[0] // 3:] for i, x in enumerate(data)}
+        b2.append(half)
+        b2.append({i: x for i, x in rest.items() if x.shape[0] > 0})
+        for i in range(len(specs)):
+            np.testing.assert_array_equal(b1.sketch(i), b2.sketch(i))
+
+
+def test_batch_equals_single_handles():
+    """Each sketch in the mix gives the result it gives alone (single handle,
+    FP32 path) within the parity tolerance."""
+    specs = _specs(12, 11)
+    data = [W.random_noisy(n, d, m=4, seed=50 + i, dtype=np.float32)
+            for i, (d, e, n) in enumerate(specs)]
+    with fd.FDBatch([s[0] for s in specs], [s[1] for s in specs]) as b:
+        b.append({i: torch.from_numpy(a).cuda() for i, a in enumerate(data)})
+        for i, (d, e, n) in enumerate(specs):
+            with fd.FDSketch(d, e, "fd", 1.0, "fp32") as s:
+                s.append(torch.from_numpy(data[i]).cuda())
+                Bs = s.sketch()
+            Bb = b.sketch(i)
+            na2 = float(np.sum(data[i].astype(np.float64) ** 2))
+            assert_sigma_parity(Bb, Bs, na2, "fp32", what=f"mix vs solo {i}")
+            assert abs(cov_err(data[i], Bb) - cov_err(data[i], Bs)) <= COV_ABS
+
+
+def test_batch_rejects_bad_items():
+    with fd.FDBatch([64, 64], [4, 4]) as b:
+        x = torch.zeros(10, 64, device="cuda")
+        with pytest.raises(fd.FDError):
+            b.append({5: x})
+    with pytest.raises(fd.FDError):
+        fd.FDBatch([64], [65])    # 2*ell > 128
