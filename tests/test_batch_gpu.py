@@ -33,8 +33,11 @@ def _specs(k, seed):
 def test_batch_matches_oracle(variant):
     alpha = 0.2 if variant == "pfd" else 1.0
     specs = _specs(24, 7)
-    if variant == "ss":   # SS parity on short streams (discrete merge choices)
-        specs = [(d, e, min(n, 2 * e + 2 * (e + 1) + 3)) for d, e, n in specs]
+    if variant == "ss":
+        # SS takes discrete merge decisions that a near-tie can flip (design
+        # reading P13): element-wise parity on exactly one reduction; the
+        # longer streams are checked by SS's invariant in test_batch_ss_mass
+        specs = [(d, e, 2 * e) for d, e, n in specs]
     data = [W.random_noisy(n, d, m=max(1, e // 2), seed=100 + i, dtype="bf16")
             for i, (d, e, n) in enumerate(specs)]
     with fd.FDBatch([s[0] for s in specs], [s[1] for s in specs], variant, alpha) as b:
@@ -48,6 +51,19 @@ def test_batch_matches_oracle(variant):
             st = b.stats(i)
             assert abs(st["norm_a2"] - io["normA2"]) <= 1e-12 * io["normA2"]
             assert st["n_seen"] == n
+
+
+def test_batch_ss_mass():
+    """SpaceSaving Directions keep ||B||_F^2 = ||A||_F^2 (Theorem, Sec. 3.1)."""
+    specs = _specs(16, 13)
+    data = [W.random_noisy(n, d, m=max(1, e // 2), seed=300 + i, dtype=np.float32)
+            for i, (d, e, n) in enumerate(specs)]
+    with fd.FDBatch([s[0] for s in specs], [s[1] for s in specs], "ss") as b:
+        b.append({i: torch.from_numpy(a).cuda() for i, a in enumerate(data)})
+        for i in range(len(specs)):
+            B = b.sketch(i)
+            na2 = float(np.sum(data[i].astype(np.float64) ** 2))
+            assert abs(float(np.sum(B * B)) - na2) <= 1e-5 * na2
 
 
 def test_batch_split_appends_bit_identical():
