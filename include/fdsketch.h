@@ -71,7 +71,8 @@ enum {
                       of the last one */
   FD_ENOCONV = -4, /* an eigensolve reached its sweep cap; the result is still
                       written and the count is in fd_stats_t.noconv */
-  FD_EBUSY = -5    /* serving: no room to admit the request now */
+  FD_EBUSY = -5,   /* serving: no room to admit the request now */
+  FD_ETOOBIG = -6  /* a size exceeds the fixed workspace of fd_cov_err_noalloc */
 };
 
 #define FD_MAX_BUFFER_ROWS 512 /* 2*ell limit of one sketch */
@@ -134,6 +135,31 @@ int fd_cov_err_pair(const void* A, int64_t n, int64_t d, int64_t lda, int32_t a_
                     const void* B, int64_t rows, int32_t b_dtype, int32_t on_device,
                     void* cuda_stream, double* cov_err, double* lambda_min,
                     double* lambda_max);
+
+/* The covariance-error evaluator of fd_cov_err_pair for callers that cannot
+ * allocate device memory: code that runs inside a custom device allocator or
+ * a memory-pool callback (a nested cudaMalloc would re-enter it), runtimes
+ * that account for every byte of device memory themselves, and servers that
+ * forbid allocation once they are up. The paper has no counterpart; this is
+ * a deployment variant of the evaluator.
+ *
+ * A (n x d, row stride lda) and B (rows x d, contiguous) are device pointers
+ * (FP32 or FP64 per dtype); *cov_err (host) receives the value. No device or
+ * pinned memory is allocated: every intermediate vector lives in one
+ * file-scope device array of about 4.6 MB, which each GPU that loads the
+ * library keeps until the process exits. Limits: d <= FD_NOALLOC_MAX_D,
+ * rows <= FD_NOALLOC_MAX_B_ROWS, at most FD_NOALLOC_MAX_STEPS Lanczos steps
+ * (the value is then the estimate after that many steps); larger sizes return
+ * FD_ETOOBIG. The first call on a device looks up the array's device address
+ * (make it before any stream capture). Every call shares the array and clears
+ * it first, so calls that overlap on the GPU (several streams or threads at
+ * once) race: serialise them. Synchronises `cuda_stream`. */
+#define FD_NOALLOC_MAX_D 1024
+#define FD_NOALLOC_MAX_B_ROWS 512
+#define FD_NOALLOC_MAX_STEPS 256
+int fd_cov_err_noalloc(const void* A, int64_t n, int64_t d, int64_t lda, int32_t a_dtype,
+                       const void* B, int64_t rows, int32_t b_dtype, void* cuda_stream,
+                       double* cov_err);
 
 /* Counters of the handle (synchronises the stream). */
 int fd_stats(fd_handle h, fd_stats_t* s);

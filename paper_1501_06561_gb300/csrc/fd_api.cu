@@ -591,6 +591,7 @@ extern "C" const char* fd_strerror(int32_t code) {
     case FD_ECUDA: return cuda_error_text();
     case FD_ENOCONV: return "eigensolve reached its sweep cap";
     case FD_EBUSY: return "no room to admit the request";
+    case FD_ETOOBIG: return "size exceeds the fixed workspace of the no-allocation evaluator";
     default: return "unknown error code";
   }
 }

@@ -22,7 +22,7 @@ VARIANT = {"fd": 0, "pfd": 1, "ss": 2, "isvd": 3}
 PREC = {"fp32": 0, "bf16x3": 1, "fp64": 2}
 F32, BF16, F64 = 0, 1, 2
 ERR = {0: "FD_OK", -1: "FD_EINVAL", -2: "FD_ENOMEM", -3: "FD_ECUDA", -4: "FD_ENOCONV",
-       -5: "FD_EBUSY"}
+       -5: "FD_EBUSY", -6: "FD_ETOOBIG"}
 
 _lib = None
 
@@ -80,6 +80,7 @@ def load():
         "fd_batch_stats": [vp, i32, ctypes.POINTER(Stats)],
         "fd_batch_sketch_all": [vp, vp, ctypes.POINTER(i64)],
         "fd_batch_reset": [vp],
+        "fd_cov_err_noalloc": [vp, i64, i64, i64, i32, vp, i64, i32, vp, ctypes.POINTER(dbl)],
         "fd_batch_destroy": [vp],
         "fd_version": [],
     }
@@ -222,6 +223,20 @@ class FDSketch:
             self.close()
         except Exception:
             pass
+
+
+def cov_err_noalloc(A, B, stream=None):
+    """cov-err of CUDA tensors A and B through fd_cov_err_noalloc (no device
+    allocation inside the library; fixed workspace, d <= 1024)."""
+    pa, n, lda, ca, da, ka = _as_rows(A)
+    pb, rows, ldb, cb, db, kb = _as_rows(B)
+    if not (da and db):
+        raise ValueError("A and B must be CUDA tensors")
+    d = A.shape[1]
+    out = ctypes.c_double()
+    _check(load().fd_cov_err_noalloc(pa, n, d, lda, ca, pb, rows, cb, _stream_ptr(stream),
+                                     ctypes.byref(out)), "fd_cov_err_noalloc")
+    return out.value
 
 
 def cov_err_pair(A, B, stream=None):
