@@ -34,6 +34,10 @@ WORKLOADS = {
                prec="bf16x3", name="random-noisy n=200000 d=2000 k=50 zeta=10 fp32 rows"),
     "c0": dict(n=10_000, d=500, m=30, zeta=10.0, seed=0, ell=50, variant="fd", alpha=1.0,
                prec="fp32", name="random-noisy n=10000 d=500 m=30 zeta=10"),
+    "c4": dict(count=10_000, d=512, ell=32, rate=5e6, seconds=10.0, warm=1.0, seed=4,
+               variant="fd", alpha=1.0, prec="fp32", n=None,
+               name="serving: 10000 live sketches d=512 ell=32, Poisson row blocks of "
+                    "log-uniform size 1..4096, sparse non-negative rows (2%), 5M rows/s offered"),
     "c3": dict(count=4096, seed=3, variant="fd", alpha=1.0, prec="fp32", ell=None, n=None,
                name="batched: 4096 random-noisy streams, d in U{64..1024}, ell in U{16..64}, "
                     "n in U{1000..50000}, k = ell/2, bf16 rows"),
@@ -63,7 +67,7 @@ def parse():
 
 def config(args):
     w = dict(WORKLOADS[args.workload])
-    if args.workload == "c3":
+    if args.workload in ("c3", "c4"):
         for k in ("variant", "alpha"):
             if getattr(args, k) is not None:
                 w[k] = getattr(args, k)
@@ -422,6 +426,80 @@ def cpu_baseline_batch(specs, flat, views, w, budget_s=20.0):
             "sample": f"{len(used)} of the batch's streams (ids {used}, {rows} rows, {t:.1f} s)"}
 
 
+def run_serve(args, w):
+    """Serving workload: an open-loop Poisson generator submits row blocks to
+    the continuous-batching server; reports achieved rows/s and the p50/p99
+    latency from submit to completion."""
+    import numpy as np
+    from paper_1501_06561_gb300 import fd, workloads
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    fd.load()
+    count = args.count or w["count"]
+    rng = np.random.default_rng(w["seed"] + rank)
+    pool = workloads.sparse_nonneg_rows(1 << 19, d=w["d"], seed=w["seed"] + rank)
+    mean_rows = (4096 - 1) / np.log(4096)
+    req_rate = w["rate"] / mean_rows
+    srv = fd.FDServer(count, w["d"], w["ell"], w["variant"], w["alpha"],
+                      budget_bytes=1 << 30, streams=4)
+    total = w["warm"] + w["seconds"]
+    t_start = time.perf_counter()
+    t_next = t_start
+    pos = 0
+    backlog = []
+    submitted_rows = 0
+    warm_tickets = set()
+    while True:
+        now = time.perf_counter()
+        if now - t_start > total:
+            break
+        while t_next <= now:
+            n = int(min(4096, max(1, np.exp(rng.uniform(0, np.log(4096))))))
+            sid = int(rng.integers(0, count))
+            if pos + n > pool.shape[0]:
+                pos = 0
+            backlog.append((sid, pos, n, t_next))
+            pos += n
+            t_next += rng.exponential(1.0 / req_rate)
+        keep = []
+        for sid, p0, n, ta in backlog:
+            t = srv.submit(sid, pool[p0:p0 + n])
+            if t is None:
+                keep.append((sid, p0, n, ta))
+                continue
+            submitted_rows += n
+            if ta - t_start < w["warm"]:
+                warm_tickets.add(t)
+        backlog = keep
+    t_end = time.perf_counter()
+    srv.drain()
+    t_drain = time.perf_counter()
+    done = srv.poll(1 << 22)
+    lat = np.array([l for t, l in done if t not in warm_tickets]) * 1e3
+    c = srv.counters()
+    srv.close()
+    if rank != 0:
+        return 0
+    rows_done = c["rows_done"]
+    line = {"metric": "serving append latency p99 (ms) and rows/s", "value": rows_done / (t_drain - t_start),
+            "unit": "rows/s", "n_gpus": world, "steps": 1, "warmup": 0,
+            "ms_per_step": (t_drain - t_start) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32, f64 shrink", "data": "synthetic",
+            "config": {"workload": w["name"], "sketches": count, "offered_rows_per_s": w["rate"],
+                       "seconds": w["seconds"], "warm_s": w["warm"]},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)) if lat.size else None,
+                           "p99": float(np.percentile(lat, 99)) if lat.size else None,
+                           "requests": int(lat.size)},
+            "server": c, "backlog_left": len(backlog),
+            "e2e": {"value": rows_done / (t_drain - t_start), "unit": "rows/s",
+                    "h2d_bytes_per_step": int(submitted_rows * w["d"] * 4),
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": c["launches"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     w = config(args)
@@ -429,6 +507,8 @@ def main():
         return run_reference(args, w)
     if args.workload == "c3":
         return run_batch(args, w)
+    if args.workload == "c4":
+        return run_serve(args, w)
     import numpy as np
     import torch
     from paper_1501_06561_gb300 import fd

@@ -218,6 +218,32 @@ int fd_batch_stats(fd_batch b, int32_t id, fd_stats_t* s);
 int fd_batch_reset(fd_batch b);
 int fd_batch_destroy(fd_batch b);
 
+/* ---- Serving: continuous batching of append requests --------------------
+ * A request loop over `count` live sketches of one shape (d, ell). A request
+ * (sketch id, n host rows of d FP32 values) is admitted when it fits the
+ * device-memory budget (budget_bytes of pinned host plus device staging);
+ * otherwise fd_serve_submit returns FD_EBUSY and the caller retries. A native
+ * engine thread launches one batched update (the fd_batch kernel) over every
+ * admitted request whose sketch is not already on the GPU, on the next of
+ * `streams` streams, so launches overlap on the device while each sketch is
+ * in at most one launch; requests of one sketch are applied in submit order.
+ * Per sketch the result is that of fd_append of the same rows in that order.
+ * The paper has no serving layer; the arithmetic is Algorithm 1's. */
+typedef struct fd_server_state* fd_server;
+int fd_serve_create(int32_t count, int64_t d, int32_t ell, int32_t variant, double alpha,
+                    int64_t budget_bytes, int32_t streams, fd_server* out);
+/* Copies the rows (row stride d) into staging before returning. */
+int fd_serve_submit(fd_server s, int32_t id, const float* rows, int64_t n, int64_t* ticket);
+/* Up to `max` completed requests since the last poll: tickets and their
+ * latency in seconds (submit to completion seen by the engine). */
+int fd_serve_poll(fd_server s, int64_t* tickets, double* latency_s, int32_t max, int32_t* count);
+int fd_serve_drain(fd_server s);
+/* Sketch `id` (ell x d, host out) after every submitted request is done. */
+int fd_serve_sketch(fd_server s, int32_t id, void* out, int32_t dtype);
+int fd_serve_counters(fd_server s, int64_t* admitted, int64_t* busy, int64_t* launches,
+                      int64_t* rows_done);
+int fd_serve_destroy(fd_server s);
+
 /* Text for an FD_E* code (static storage). */
 const char* fd_strerror(int32_t code);
 

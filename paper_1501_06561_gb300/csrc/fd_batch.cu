@@ -23,7 +23,8 @@ namespace fdk {
 
 namespace {
 
-constexpr int BT = 512;           // threads per CTA
+constexpr int BT = 256;           // threads per CTA
+constexpr int GB = (528 + BT - 1) / BT;  // Gram 4x4 blocks per thread (<= 528 blocks)
 constexpr int BMAX_L = 128;       // largest buffer (2*ell) a batched sketch may have
 constexpr int KCH = 32;           // Gram K chunk
 constexpr int RCH = 64;           // rotate column chunk
@@ -70,21 +71,22 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
   float* Bst = reinterpret_cast<float*>(smem + REG_A);
   unsigned char* sc = smem + REG_A + REG_B;
   const int np = nrows + (nrows & 1);
-  const int ld = (np + 3) & ~3;
+  const int npb = (np + 7) & ~7;  // block Jacobi pads to whole 4-column block pairs
+  const int ld = npb;
   const long long d = S.d, ldb = S.ldb;
   const float* buf = S.buf;
 
   // ---- Gram G = B B^T (upper 4x4 blocks, K in chunks of KCH staged in Bst) ----
   const int nb4 = (np + 3) / 4;
   const int nblk = nb4 * (nb4 + 1) / 2;
-  float acc[2][16];
+  float acc[GB][16];
 #pragma unroll
-  for (int u = 0; u < 2; ++u)
+  for (int u = 0; u < GB; ++u)
 #pragma unroll
     for (int e = 0; e < 16; ++e) acc[u][e] = 0.f;
-  int bi[2], bj[2];
+  int bi[GB], bj[GB];
 #pragma unroll
-  for (int u = 0; u < 2; ++u) {
+  for (int u = 0; u < GB; ++u) {
     int b = tid + u * BT;
     bi[u] = -1;
     bj[u] = -1;
@@ -105,7 +107,7 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < GB; ++u) {
       if (bi[u] < 0) continue;
       const int i0 = bi[u] * 4, j0 = bj[u] * 4;
 #pragma unroll 8
@@ -123,10 +125,10 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
   }
   __syncthreads();
   // write G (both triangles) into A with stride ld, zero padding
-  for (int idx = tid; idx < np * ld; idx += BT) A[idx] = 0.f;
+  for (int idx = tid; idx < npb * ld; idx += BT) A[idx] = 0.f;
   __syncthreads();
 #pragma unroll
-  for (int u = 0; u < 2; ++u) {
+  for (int u = 0; u < GB; ++u) {
     if (bi[u] < 0) continue;
     const int i0 = bi[u] * 4, j0 = bj[u] * 4;
 #pragma unroll
@@ -153,7 +155,7 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
   __syncthreads();
   const float smax = s_max;
   const float inv = smax > 0.f ? 1.f / smax : 1.f;
-  for (int idx = tid; idx < np * ld; idx += BT) A[idx] *= inv;
+  for (int idx = tid; idx < npb * ld; idx += BT) A[idx] *= inv;
   float* nrm = reinterpret_cast<float*>(sc);
   double* lam = reinterpret_cast<double*>(sc + BMAX_L * 4);
   double* mu = lam + BMAX_L;
@@ -163,7 +165,9 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
   int* rrank = ord + BMAX_L;
   __syncthreads();
   int capped = 0;
-  const int sweeps = jacobi_sweeps_f32<8, 4, 1>(A, ld, np, nrm, max_sweeps, (float)tol, &capped);
+  // block Jacobi: 16-lane groups hold two 4-column blocks in registers per
+  // round (np <= 128: 16 groups, 2 float4 chunks per lane per column)
+  const int sweeps = jacobi_blocks4_f32<16, 2>(A, ld, npb, nrm, max_sweeps, (float)tol, &capped);
 
   // ---- shrink + rotate matrix (rows 0..ell-2, stride np) into Bst ----
   EigArgs a;
@@ -587,5 +591,328 @@ extern "C" int fd_batch_destroy(fd_batch_state* b) {
   cudaFree(b->doffs);
   cudaFree(b->fctr_all);
   delete b;
+  return FD_OK;
+}
+
+// ===========================================================================
+// Serving: continuous batching of append requests over many live sketches.
+//
+// Requests (sketch id, a block of rows) are admitted into a pinned host ring
+// and a device ring of the same size -- the device-memory budget. A native
+// engine thread repeatedly takes every admitted request whose sketch is not
+// already on the GPU (at most one per sketch per launch), copies their rows
+// to the device ring, and launches one batched update over all of them on the
+// next of several streams, so launches overlap on the device while sketches
+// stay consistent (a sketch is in at most one launch at a time). A launch's
+// completion releases its ring space and completes its requests; latency is
+// arrival (submit) to completion.
+// ===========================================================================
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+
+namespace {
+
+struct ServeReq {
+  int64_t ticket;
+  int id;
+  int64_t n;
+  size_t off;      // byte offset in the rings
+  size_t bytes;
+  double t_submit;
+};
+
+struct ServeLaunch {
+  cudaEvent_t ev;
+  std::vector<ServeReq> reqs;
+  int stream;
+};
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct fd_server_state {
+  fd_batch_state* b = nullptr;
+  int64_t d = 0;
+  int ell = 0;
+  size_t cap = 0;           // ring bytes
+  char* hring = nullptr;    // pinned
+  char* dring = nullptr;
+  size_t head = 0;          // next free byte; the oldest live allocation marks the tail
+  std::deque<std::pair<size_t, size_t>> allocs;  // (offset, bytes) in allocation order
+  std::vector<char> released;                    // per outstanding allocation: done?
+  int nstreams = 2;
+  std::vector<cudaStream_t> streams;
+  std::vector<BatchItem*> ditems;   // per stream
+  std::vector<BatchItem*> hitems;   // pinned, per stream
+  std::vector<int*> dnext;          // per stream
+  std::vector<char> busy_stream;
+  int next_stream = 0;
+  std::vector<char> inflight;       // per sketch
+  std::deque<ServeReq> pending;
+  std::deque<ServeLaunch> launches;
+  std::vector<std::pair<int64_t, double>> done;  // (ticket, latency s)
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread engine;
+  std::atomic<bool> stop{false};
+  int64_t next_ticket = 1;
+  int64_t admitted = 0, busy = 0, launched = 0, rows_done = 0;
+  int err = 0;
+};
+
+static void serve_release_locked(fd_server_state* s) {
+  // free ring space from the front, in allocation order
+  while (!s->allocs.empty() && s->released.front()) {
+    s->allocs.pop_front();
+    s->released.erase(s->released.begin());
+  }
+  if (s->allocs.empty()) s->head = 0;
+}
+
+// Contiguous space of `bytes` in the ring, FIFO order; false when full.
+static bool serve_ring_alloc_locked(fd_server_state* s, size_t bytes, size_t* off) {
+  if (s->allocs.empty()) {
+    if (bytes > s->cap) return false;
+    *off = 0;
+    s->head = bytes;
+    return true;
+  }
+  const size_t tail = s->allocs.front().first;
+  if (s->head > tail) {            // live bytes in [tail, head)
+    if (s->cap - s->head >= bytes) { *off = s->head; s->head += bytes; return true; }
+    if (tail >= bytes) { *off = 0; s->head = bytes; return true; }
+    return false;
+  }
+  if (s->head < tail) {            // live bytes in [tail, cap) and [0, head)
+    if (tail - s->head >= bytes) { *off = s->head; s->head += bytes; return true; }
+    return false;
+  }
+  return false;                    // head == tail with live allocations: full
+}
+
+static void serve_engine(fd_server_state* s) {
+  const double eps = 1.1920928955078125e-07;
+  while (!s->stop.load()) {
+    std::vector<ServeReq> take;
+    int st = -1;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      // completions
+      for (auto it = s->launches.begin(); it != s->launches.end();) {
+        if (cudaEventQuery(it->ev) == cudaSuccess) {
+          const double t = now_s();
+          for (auto& r : it->reqs) {
+            s->done.emplace_back(r.ticket, t - r.t_submit);
+            s->inflight[r.id] = 0;
+            s->rows_done += r.n;
+            for (size_t k = 0; k < s->allocs.size(); ++k)
+              if (s->allocs[k].first == r.off && s->allocs[k].second == r.bytes) { s->released[k] = 1; break; }
+          }
+          s->busy_stream[it->stream] = 0;
+          cudaEventDestroy(it->ev);
+          it = s->launches.erase(it);
+        } else {
+          ++it;
+        }
+      }
+      serve_release_locked(s);
+      // a free stream?
+      for (int k = 0; k < s->nstreams; ++k) {
+        const int c = (s->next_stream + k) % s->nstreams;
+        if (!s->busy_stream[c]) { st = c; break; }
+      }
+      if (st >= 0) {
+        std::vector<char> picked(s->inflight.size(), 0);
+        for (auto it = s->pending.begin(); it != s->pending.end();) {
+          if (!s->inflight[it->id] && !picked[it->id]) {
+            picked[it->id] = 1;
+            take.push_back(*it);
+            it = s->pending.erase(it);
+          } else {
+            ++it;
+          }
+        }
+        for (auto& r : take) s->inflight[r.id] = 1;
+        if (!take.empty()) {
+          s->busy_stream[st] = 1;
+          s->next_stream = (st + 1) % s->nstreams;
+        }
+      }
+      if (take.empty()) {
+        s->cv.wait_for(lk, std::chrono::microseconds(20));
+        continue;
+      }
+    }
+    // launch outside the lock
+    cudaStream_t stream = s->streams[st];
+    BatchItem* hi = s->hitems[st];
+    const int ns = (int)take.size();
+    for (int i = 0; i < ns; ++i) {
+      const ServeReq& r = take[i];
+      cudaMemcpyAsync(s->dring + r.off, s->hring + r.off, r.bytes, cudaMemcpyHostToDevice, stream);
+      hi[i] = BatchItem{r.id, FD_F32, s->dring + r.off, r.n, s->d};
+    }
+    cudaMemcpyAsync(s->ditems[st], hi, (size_t)ns * sizeof(BatchItem), cudaMemcpyHostToDevice, stream);
+    cudaMemsetAsync(s->dnext[st], 0, sizeof(int), stream);
+    const int grid = std::min(ns, 2 * s->b->nsm);
+    batch_kernel<<<grid, BT, BATCH_SMEM, stream>>>(s->b->dsk, s->ditems[st], ns, s->dnext[st],
+                                                   s->b->variant, s->b->alpha, s->b->max_sweeps,
+                                                   4.0 * eps * std::sqrt((double)BMAX_L));
+    ServeLaunch L;
+    cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming);
+    cudaEventRecord(L.ev, stream);
+    L.reqs = std::move(take);
+    L.stream = st;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      for (auto& r : L.reqs) {
+        int64_t m = s->b->m[r.id] + r.n;
+        const int Lr = 2 * s->b->ell[r.id];
+        if (m >= Lr) m = (s->b->ell[r.id] - 1) + (m - Lr) % (s->b->ell[r.id] + 1);
+        s->b->m[r.id] = (int)m;
+        s->b->nseen[r.id] += r.n;
+      }
+      s->launched += 1;
+      s->launches.push_back(std::move(L));
+    }
+    if (cudaGetLastError() != cudaSuccess) s->err = 1;
+  }
+}
+
+extern "C" int fd_serve_destroy(fd_server_state* s);
+
+extern "C" int fd_serve_create(int32_t count, int64_t d, int32_t ell, int32_t variant,
+                               double alpha, int64_t budget_bytes, int32_t nstreams,
+                               fd_server_state** out) {
+  if (!out || count < 1 || d < 1 || budget_bytes < d * 4 || nstreams < 1 || nstreams > 8)
+    return FD_EINVAL;
+  *out = nullptr;
+  std::vector<int64_t> ds(count, d);
+  std::vector<int32_t> es(count, ell);
+  fd_server_state* s = new (std::nothrow) fd_server_state();
+  if (!s) return FD_ENOMEM;
+  int rc = fd_batch_create(count, ds.data(), es.data(), variant, alpha, FD_PREC_FP32, nullptr, &s->b);
+  if (rc != FD_OK) { delete s; return rc; }
+  s->d = d;
+  s->ell = ell;
+  s->cap = (size_t)budget_bytes;
+  s->nstreams = nstreams;
+  cudaError_t e = cudaMallocHost(&s->hring, s->cap);
+  if (e == cudaSuccess) e = cudaMalloc(&s->dring, s->cap);
+  s->streams.resize(nstreams);
+  s->ditems.resize(nstreams);
+  s->hitems.resize(nstreams);
+  s->dnext.resize(nstreams);
+  s->busy_stream.assign(nstreams, 0);
+  for (int k = 0; k < nstreams && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&s->ditems[k], (size_t)count * sizeof(BatchItem));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->hitems[k], (size_t)count * sizeof(BatchItem));
+    if (e == cudaSuccess) e = cudaMalloc(&s->dnext[k], sizeof(int));
+  }
+  if (e != cudaSuccess) {
+    set_cuda_error(e, "fd_serve_create");
+    fd_serve_destroy(s);
+    return FD_ENOMEM;
+  }
+  s->inflight.assign(count, 0);
+  s->engine = std::thread(serve_engine, s);
+  *out = s;
+  return FD_OK;
+}
+
+extern "C" int fd_serve_submit(fd_server_state* s, int32_t id, const float* rows, int64_t n,
+                               int64_t* ticket) {
+  if (!s || !rows || n < 1 || !ticket || id < 0 || id >= s->b->count) return FD_EINVAL;
+  const size_t bytes = (size_t)n * s->d * 4;
+  if (bytes > s->cap) return FD_EINVAL;
+  size_t off = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!serve_ring_alloc_locked(s, bytes, &off)) { s->busy += 1; return FD_EBUSY; }
+    s->allocs.emplace_back(off, bytes);
+    s->released.push_back(0);
+    *ticket = s->next_ticket++;
+    s->admitted += 1;
+  }
+  std::memcpy(s->hring + off, rows, bytes);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->pending.push_back(ServeReq{*ticket, id, n, off, bytes, now_s()});
+  }
+  s->cv.notify_one();
+  return FD_OK;
+}
+
+extern "C" int fd_serve_poll(fd_server_state* s, int64_t* tickets, double* latency_s, int32_t max,
+                             int32_t* count) {
+  if (!s || !count || max < 0 || (max > 0 && (!tickets || !latency_s))) return FD_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  const int k = (int)std::min<size_t>((size_t)max, s->done.size());
+  for (int i = 0; i < k; ++i) {
+    tickets[i] = s->done[i].first;
+    latency_s[i] = s->done[i].second;
+  }
+  s->done.erase(s->done.begin(), s->done.begin() + k);
+  *count = k;
+  return s->err ? FD_ECUDA : FD_OK;
+}
+
+extern "C" int fd_serve_drain(fd_server_state* s) {
+  if (!s) return FD_EINVAL;
+  for (;;) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (s->pending.empty() && s->launches.empty()) break;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  return s->err ? FD_ECUDA : FD_OK;
+}
+
+extern "C" int fd_serve_sketch(fd_server_state* s, int32_t id, void* out, int32_t dtype) {
+  if (!s) return FD_EINVAL;
+  int rc = fd_serve_drain(s);
+  if (rc != FD_OK) return rc;
+  cudaDeviceSynchronize();
+  return fd_batch_sketch(s->b, id, out, dtype, 0);
+}
+
+extern "C" int fd_serve_counters(fd_server_state* s, int64_t* admitted, int64_t* busy,
+                                 int64_t* launches, int64_t* rows_done) {
+  if (!s) return FD_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (admitted) *admitted = s->admitted;
+  if (busy) *busy = s->busy;
+  if (launches) *launches = s->launched;
+  if (rows_done) *rows_done = s->rows_done;
+  return FD_OK;
+}
+
+extern "C" int fd_serve_destroy(fd_server_state* s) {
+  if (!s) return FD_EINVAL;
+  if (s->engine.joinable()) {
+    fd_serve_drain(s);
+    s->stop.store(true);
+    s->cv.notify_all();
+    s->engine.join();
+  }
+  for (auto& L : s->launches) cudaEventDestroy(L.ev);
+  for (int k = 0; k < (int)s->streams.size(); ++k) {
+    if (s->streams[k]) { cudaStreamSynchronize(s->streams[k]); cudaStreamDestroy(s->streams[k]); }
+    cudaFree(s->ditems[k]);
+    if (s->hitems[k]) cudaFreeHost(s->hitems[k]);
+    cudaFree(s->dnext[k]);
+  }
+  if (s->hring) cudaFreeHost(s->hring);
+  cudaFree(s->dring);
+  if (s->b) fd_batch_destroy(s->b);
+  delete s;
   return FD_OK;
 }

@@ -81,6 +81,14 @@ def load():
         "fd_batch_sketch_all": [vp, vp, ctypes.POINTER(i64)],
         "fd_batch_reset": [vp],
         "fd_cov_err_noalloc": [vp, i64, i64, i64, i32, vp, i64, i32, vp, ctypes.POINTER(dbl)],
+        "fd_serve_create": [i32, i64, i32, i32, dbl, i64, i32, ctypes.POINTER(vp)],
+        "fd_serve_submit": [vp, i32, vp, i64, ctypes.POINTER(i64)],
+        "fd_serve_poll": [vp, ctypes.POINTER(i64), ctypes.POINTER(dbl), i32, ctypes.POINTER(i32)],
+        "fd_serve_drain": [vp],
+        "fd_serve_sketch": [vp, i32, vp, i32],
+        "fd_serve_counters": [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                              ctypes.POINTER(i64)],
+        "fd_serve_destroy": [vp],
         "fd_batch_destroy": [vp],
         "fd_version": [],
     }
@@ -341,6 +349,68 @@ class FDBatch:
     def close(self):
         if getattr(self, "_h", None):
             load().fd_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FDServer:
+    """Continuous-batching request loop over `count` live sketches (fd_serve_*)."""
+
+    def __init__(self, count: int, d: int, ell: int, variant: str = "fd", alpha: float = 1.0,
+                 budget_bytes: int = 256 << 20, streams: int = 2):
+        lib = load()
+        self.count, self.d, self.ell = count, d, ell
+        h = ctypes.c_void_p()
+        _check(lib.fd_serve_create(count, d, ell, VARIANT[variant], float(alpha), int(budget_bytes),
+                                   streams, ctypes.byref(h)), "fd_serve_create")
+        self._h = h
+
+    def submit(self, sid: int, rows):
+        """Ticket, or None when the budget is full (FD_EBUSY: retry later)."""
+        a = np.ascontiguousarray(rows, dtype=np.float32)
+        t = ctypes.c_int64()
+        rc = load().fd_serve_submit(self._h, sid, ctypes.c_void_p(a.ctypes.data), a.shape[0],
+                                    ctypes.byref(t))
+        if rc == -5:
+            return None
+        _check(rc, "fd_serve_submit")
+        return t.value
+
+    def poll(self, max_items: int = 65536):
+        tk = (ctypes.c_int64 * max_items)()
+        lat = (ctypes.c_double * max_items)()
+        cnt = ctypes.c_int32()
+        _check(load().fd_serve_poll(self._h, tk, lat, max_items, ctypes.byref(cnt)), "fd_serve_poll")
+        return [(tk[i], lat[i]) for i in range(cnt.value)]
+
+    def drain(self):
+        _check(load().fd_serve_drain(self._h), "fd_serve_drain")
+
+    def sketch(self, sid: int):
+        B = np.empty((self.ell, self.d), dtype=np.float64)
+        _check(load().fd_serve_sketch(self._h, sid, ctypes.c_void_p(B.ctypes.data), F64),
+               "fd_serve_sketch")
+        return B
+
+    def counters(self):
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(load().fd_serve_counters(self._h, *[ctypes.byref(x) for x in v]), "fd_serve_counters")
+        return dict(zip(("admitted", "busy", "launches", "rows_done"), [x.value for x in v]))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fd_serve_destroy(self._h)
             self._h = None
 
     def __enter__(self):
