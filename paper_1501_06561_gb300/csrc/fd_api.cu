@@ -278,6 +278,7 @@ static int reduce_rows(fd_state* h, int nrows, void* out, int64_t ldo, DevCounte
   a.max_sweeps = h->max_sweeps;
   a.tol = h->tol;
   a.symmetrize = 1;
+  a.use_tri = 1;
   if (h->prec == FD_PREC_BF16X3) {
     int rc;
     { ProfScope ps(h, FD_K_GRAM); rc = tc_gram(h->tc, nrows); }

@@ -18,6 +18,7 @@
 #include "fd_internal.cuh"
 #include "fd_eig.cuh"
 #include "fd_jacobi.cuh"
+#include "fd_tridiag.cuh"
 
 namespace fdk {
 
@@ -56,10 +57,13 @@ __device__ __forceinline__ double load_as_f64(const void* p, long long idx, int 
 
 // Shared memory map (bytes): region A 64 KB (Jacobi matrix / rotate staging),
 // region B 32 KB (Gram staging / rotate matrix), scalars.
-constexpr size_t REG_A = (size_t)BMAX_L * BMAX_L * 4;
+constexpr int TRI_NB = 16;        // inverse-iteration vectors per batch
+constexpr size_t REG_A = ((size_t)BMAX_L * (BMAX_L | 1) * 4 + 15) / 16 * 16;
 constexpr size_t REG_B = (size_t)BMAX_L * RCH * 4;
 constexpr size_t SCAL = (size_t)BMAX_L * (4 * sizeof(double) + 2 * sizeof(int)) + BMAX_L * 4 + 256;
-constexpr size_t BATCH_SMEM = REG_A + REG_B + SCAL;
+constexpr size_t REST = (REG_B + SCAL > tri_rest_bytes(BMAX_L, TRI_NB)) ? REG_B + SCAL
+                                                                       : tri_rest_bytes(BMAX_L, TRI_NB);
+constexpr size_t BATCH_SMEM = REG_A + REST;
 
 // One reduction of the first `nrows` rows of S.buf; new rows 0..ell-2 go to
 // `out` (stride ldo; may be S.buf itself), counters from cin to cout.
@@ -72,7 +76,10 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
   unsigned char* sc = smem + REG_A + REG_B;
   const int np = nrows + (nrows & 1);
   const int npb = (np + 7) & ~7;  // block Jacobi pads to whole 4-column block pairs
-  const int ld = npb;
+  // full buffers take the tridiagonal eigensolve (odd stride), flushes Jacobi
+  const bool tri = (nrows == 2 * S.ell) && nrows >= 4;
+  const int ld = tri ? (nrows | 1) : npb;
+  const int nz = tri ? nrows : npb;  // rows of A in use
   const long long d = S.d, ldb = S.ldb;
   const float* buf = S.buf;
 
@@ -125,7 +132,7 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
   }
   __syncthreads();
   // write G (both triangles) into A with stride ld, zero padding
-  for (int idx = tid; idx < npb * ld; idx += BT) A[idx] = 0.f;
+  for (int idx = tid; idx < nz * ld; idx += BT) A[idx] = 0.f;
   __syncthreads();
 #pragma unroll
   for (int u = 0; u < GB; ++u) {
@@ -155,7 +162,22 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
   __syncthreads();
   const float smax = s_max;
   const float inv = smax > 0.f ? 1.f / smax : 1.f;
-  for (int idx = tid; idx < npb * ld; idx += BT) A[idx] *= inv;
+  for (int idx = tid; idx < nz * ld; idx += BT) A[idx] *= inv;
+  __syncthreads();
+  if (tri) {
+    EigArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = nrows;
+    a.ell = S.ell;
+    a.variant = variant;
+    a.alpha = alpha;
+    a.ctr_in = cin;
+    a.ctr_out = cout;
+    a.wrot = Bst;  // written last, over the dead inverse-iteration bands
+    a.ldr = np;
+    a.max_sweeps = max_sweeps;
+    tri_eig_shrink<TRI_NB, 8>(a, A, ld, nrows, smax > 0.f ? (double)smax : 1.0, smem + REG_A);
+  } else {
   float* nrm = reinterpret_cast<float*>(sc);
   double* lam = reinterpret_cast<double*>(sc + BMAX_L * 4);
   double* mu = lam + BMAX_L;
@@ -184,6 +206,7 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
   __syncthreads();
   eig_finish<float>(a, A, ld, nrows, np, sweeps, capped, smax > 0.f ? (double)smax : 1.0, lam,
                     mu, mup, scl, ord, rrank);
+  }
   __syncthreads();
 
   // ---- rotate: out[r][c] = sum_i W[r][i] B[i][c], column chunks staged in A ----

@@ -56,45 +56,20 @@ __device__ void eig_load(const EigArgs& a, T* Wm, int ld, int n, int np) {
 
 // Steps after the Jacobi sweeps: eigenvalues, sort, ReduceRank (FP64),
 // rotate matrix, counters. `sweep` = sweeps run (== max_sweeps if capped).
-template <typename T>
-__device__ void eig_finish(const EigArgs& a, const T* Wm, int ld, int n, int np, int sweep,
-                           int capped, double wscale, double* lam, double* mu, double* mup,
-                           double* scl, int* ord, int* rrank) {
+// ReduceRank in FP64 on the masses mu_k = sigma_k^2 sorted descending
+// (k = 0..n-1; entries n..np-1 are padding): writes sigma'^2 to mup and the
+// output rank of every retained position (-1 if freed) to rrank; returns the
+// number of retained positions and the deltas subtracted through dsum_out /
+// dlast_out (shared). `eps_arith` is the unit of the eigensolve's arithmetic
+// (SS treats masses at or below np * eps_arith * mu_0 as empty).
+static __device__ void shrink_sorted(const EigArgs& a, int n, int np, double eps_arith, const double* mu,
+                              double* mup, int* rrank, int* count_out, double* dsum_out,
+                              double* dlast_out) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nwarps = blockDim.x >> 5;
-  __shared__ int s_count;
   __shared__ double s_dsum, s_dlast;
-  const int s_sweeps = sweep;
-  // lambda_j = ||w_j|| in FP64 (one warp per column).
-  for (int j = warp; j < np; j += nwarps) {
-    double s = 0.0;
-    for (int i = lane; i < np; i += 32) {
-      const double v = (double)Wm[(int64_t)j * ld + i];
-      s = fma(v, v, s);
-    }
-    s = warp_sum(s);
-    if (lane == 0) lam[j] = (j < n) ? sqrt(s) * wscale : -1.0;  // padding column sorts last
-  }
-  __syncthreads();
-
-  // 4. Sort descending, ties by column index.
-  for (int j = tid; j < np; j += blockDim.x) {
-    const double lj = lam[j];
-    int rank = 0;
-    for (int i = 0; i < np; ++i) {
-      const double li = lam[i];
-      rank += (li > lj) || (li == lj && i < j);
-    }
-    ord[rank] = j;
-  }
-  __syncthreads();
-  for (int k = tid; k < np; k += blockDim.x) {
-    const double v = lam[ord[k]];
-    mu[k] = v > 0.0 ? v : 0.0;
-  }
+  __shared__ int s_count;
   if (tid == 0) { s_dsum = 0.0; s_dlast = 0.0; }
   __syncthreads();
-
   // 5. ReduceRank in FP64 on the masses mu_k = sigma_k^2 (k = 0..n-1 sorted).
   const int ell = a.ell;
   if (a.variant != FD_VAR_SS) {
@@ -120,7 +95,7 @@ __device__ void eig_finish(const EigArgs& a, const T* Wm, int ld, int n, int np,
     // SS (Algorithm 3, repeated): masses at or below the numerical-rank floor
     // are empty; then merge the second-smallest into the smallest until ell-1
     // directions remain. Ties: the larger sorted position counts as smaller.
-    const double flo = mu[0] * (double)np * Eps<T>::v;
+    const double flo = mu[0] * (double)np * eps_arith;
     for (int k = lane; k < np; k += 32) mup[k] = (k < n && mu[k] > flo) ? mu[k] : 0.0;
     __syncwarp();
     int alive = 0;
@@ -191,8 +166,6 @@ __device__ void eig_finish(const EigArgs& a, const T* Wm, int ld, int n, int np,
       }
     }
     rrank[k] = rank;
-    // scale of column w_j: sigma'/sigma / lambda = sqrt(mu'/mu) / mu
-    scl[k] = (v > 0.0 && mu[k] > 0.0) ? sqrt(v / mu[k]) / mu[k] : 0.0;
   }
   if (tid == 0) {
     int cnt = 0;
@@ -201,8 +174,80 @@ __device__ void eig_finish(const EigArgs& a, const T* Wm, int ld, int n, int np,
   }
   __syncthreads();
 
+  if (tid == 0) { *count_out = s_count; *dsum_out = s_dsum; *dlast_out = s_dlast; }
+  __syncthreads();
+}
+
+// FP64 bookkeeping of one reduction (thread 0) and the spectrum diagnostics.
+static __device__ void write_counters(const EigArgs& a, int n, const double* mu, const double* mup,
+                               int count, double dsum, double dlast, int capped, int sweeps) {
+  const int tid = threadIdx.x;
+  const int nout = a.ell - 1;
+  if (a.sig2_out) for (int k = tid; k < n; k += blockDim.x) { a.sig2_out[k] = mu[k]; a.sigp2_out[k] = mup[k]; }
+  if (tid == 0) {
+    DevCounters c = *a.ctr_in;
+    double rem = 0.0, nb = 0.0;
+    for (int k = 0; k < n; ++k) { rem += mu[k] - mup[k]; nb += mup[k]; }
+    c.sum_delta += dsum;
+    c.last_delta = dlast;
+    c.removed += rem;
+    c.norm_b2 = nb;
+    c.reductions += 1;
+    c.noconv += capped ? 1 : 0;
+    c.max_sweeps = fmax(c.max_sweeps, (double)sweeps);
+    c.retained = count < nout ? count : nout;
+    *a.ctr_out = c;
+  }
+}
+
+template <typename T>
+__device__ void eig_finish(const EigArgs& a, const T* Wm, int ld, int n, int np, int sweep,
+                           int capped, double wscale, double* lam, double* mu, double* mup,
+                           double* scl, int* ord, int* rrank) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = blockDim.x >> 5;
+  // lambda_j = ||w_j|| in FP64 (one warp per column).
+  for (int j = warp; j < np; j += nwarps) {
+    double s = 0.0;
+    for (int i = lane; i < np; i += 32) {
+      const double v = (double)Wm[(int64_t)j * ld + i];
+      s = fma(v, v, s);
+    }
+    s = warp_sum(s);
+    if (lane == 0) lam[j] = (j < n) ? sqrt(s) * wscale : -1.0;  // padding column sorts last
+  }
+  __syncthreads();
+
+  // 4. Sort descending, ties by column index.
+  for (int j = tid; j < np; j += blockDim.x) {
+    const double lj = lam[j];
+    int rank = 0;
+    for (int i = 0; i < np; ++i) {
+      const double li = lam[i];
+      rank += (li > lj) || (li == lj && i < j);
+    }
+    ord[rank] = j;
+  }
+  __syncthreads();
+  for (int k = tid; k < np; k += blockDim.x) {
+    const double v = lam[ord[k]];
+    mu[k] = v > 0.0 ? v : 0.0;
+  }
+  __syncthreads();
+
+  __shared__ int s_cnt;
+  __shared__ double s_ds, s_dl;
+  shrink_sorted(a, n, np, Eps<T>::v, mu, mup, rrank, &s_cnt, &s_ds, &s_dl);
+  for (int k = tid; k < np; k += blockDim.x) {
+    const double v = mup[k];
+    // scale of column w_j: sigma'/sigma / lambda = sqrt(mu'/mu) / mu
+    scl[k] = (v > 0.0 && mu[k] > 0.0) ? sqrt(v / mu[k]) / mu[k] : 0.0;
+  }
+  const int s_count = s_cnt;
+  __syncthreads();
+
   // 7. Rotate matrix rows 0..ell-2: row r = scale * w_j (zero rows past the count).
-  const int nout = ell - 1;
+  const int nout = a.ell - 1;
   T* wr = reinterpret_cast<T*>(a.wrot);
   for (int idx = tid; idx < nout * n; idx += blockDim.x) {
     const int r = idx / n, i = idx - (idx / n) * n;
@@ -231,22 +276,7 @@ __device__ void eig_finish(const EigArgs& a, const T* Wm, int ld, int n, int np,
     }
   }
 
-  // 8. FP64 bookkeeping and diagnostics.
-  if (a.sig2_out) for (int k = tid; k < n; k += blockDim.x) { a.sig2_out[k] = mu[k]; a.sigp2_out[k] = mup[k]; }
-  if (tid == 0) {
-    DevCounters c = *a.ctr_in;
-    double rem = 0.0, nb = 0.0;
-    for (int k = 0; k < n; ++k) { rem += mu[k] - mup[k]; nb += mup[k]; }
-    c.sum_delta += s_dsum;
-    c.last_delta = s_dlast;
-    c.removed += rem;
-    c.norm_b2 = nb;
-    c.reductions += 1;
-    c.noconv += capped ? 1 : 0;
-    c.max_sweeps = fmax(c.max_sweeps, (double)s_sweeps);
-    c.retained = s_count < nout ? s_count : nout;
-    *a.ctr_out = c;
-  }
+  write_counters(a, n, mu, mup, s_count, s_ds, s_dl, capped, sweep);
 }
 
 

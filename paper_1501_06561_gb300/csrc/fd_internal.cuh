@@ -48,6 +48,7 @@ struct EigArgs {
   int ldr16;
   int max_sweeps;
   double tol;          // rotate when |gamma| > tol * sqrt(alpha * beta)
+  int use_tri;         // 1: tridiagonal eigensolve where it applies (FP32)
 };
 
 // --- launchers (fd_simt.cu) -------------------------------------------------

@@ -14,6 +14,7 @@
 #include "fd_internal.cuh"
 #include "fd_jacobi.cuh"
 #include "fd_eig.cuh"
+#include "fd_tridiag.cuh"
 
 namespace fdk {
 
@@ -311,6 +312,54 @@ __global__ void __launch_bounds__(NT) eig_fast_kernel(EigArgs a) {
                     mu, mup, scl, ord, rrank);
 }
 
+// Full-buffer FP32 reductions: Householder tridiagonalisation, bisection and
+// inverse iteration (fd_tridiag.cuh), G scaled by its largest diagonal entry.
+template <int NB, int VPW>
+__global__ void __launch_bounds__(512) eig_tri_kernel(EigArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = a.n;
+  const int ld = n | 1;
+  const int tid = threadIdx.x;
+  float* A = reinterpret_cast<float*>(smem_raw);
+  __shared__ float s_max;
+  eig_load<float>(a, A, ld, n, n);
+  if (tid == 0) s_max = 0.f;
+  __syncthreads();
+  float dm = 0.f;
+  for (int i = tid; i < n; i += blockDim.x) dm = fmaxf(dm, fabsf(A[(size_t)i * ld + i]));
+  for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+  if ((tid & 31) == 0) atomicMax(reinterpret_cast<int*>(&s_max), __float_as_int(dm));
+  __syncthreads();
+  const float smax = s_max;
+  const float inv = (smax > 0.f) ? 1.f / smax : 1.f;
+  for (int idx = tid; idx < n * ld; idx += blockDim.x) A[idx] *= inv;
+  __syncthreads();
+  tri_eig_shrink<NB, VPW>(a, A, ld, n, (smax > 0.f) ? (double)smax : 1.0,
+                          smem_raw + tri_al16((size_t)n * ld * 4));
+}
+
+template <int NB, int VPW>
+cudaError_t launch_tri(const EigArgs& a, size_t smem, cudaStream_t st) {
+  static size_t attr_set = 0;
+  if (smem > attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(eig_tri_kernel<NB, VPW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = smem;
+  }
+  eig_tri_kernel<NB, VPW><<<1, 512, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Whether a reduction of n rows takes the tridiagonal eigensolve (full
+// buffers of at most 206 rows; flushes of a partial buffer keep Jacobi).
+int tri_config(int n, int ell) {
+  if (n != 2 * ell || n < 4) return 0;
+  if (n <= 128 && tri_smem_bytes(n, 32) <= 226 * 1024) return 1;
+  if (tri_smem_bytes(n, 16) <= 226 * 1024) return 2;
+  return 0;
+}
+
 size_t eig_fast_smem(int np) {
   const int ld = (np + 3) & ~3;
   return (((size_t)np * ld * 4 + 15) & ~(size_t)15) + (((size_t)np * 4 + 15) & ~(size_t)15) +
@@ -339,6 +388,11 @@ cudaError_t launch_fast(const EigArgs& a, size_t smem, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_eig_shrink(const EigArgs& a, cudaStream_t st) {
   const int np = a.n + (a.n & 1);
+  if (sizeof(T) == 4 && a.work == nullptr && a.use_tri) {
+    const int cfg = tri_config(a.n, a.ell);
+    if (cfg == 1) return launch_tri<32, 4>(a, tri_smem_bytes(a.n, 32), st);
+    if (cfg == 2) return launch_tri<16, 8>(a, tri_smem_bytes(a.n, 16), st);
+  }
   if (sizeof(T) == 4 && a.work == nullptr && np <= 224 && eig_fast_smem(np) <= 226 * 1024) {
     const size_t smem = eig_fast_smem(np);
     if (np <= 64) return launch_fast<8, 2, 1, 256>(a, smem, st);
