@@ -73,6 +73,8 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
   const int tid = threadIdx.x;
   float* A = reinterpret_cast<float*>(smem);
   float* Bst = reinterpret_cast<float*>(smem + REG_A);
+  __shared__ double s_mass[BMAX_L / 2];       // sigma'^2 of each output row
+  __shared__ float s_rsum[BT / 32][BMAX_L / 2 * RCH / BT];  // per-warp row sums of squares
   unsigned char* sc = smem + REG_A + REG_B;
   const int np = nrows + (nrows & 1);
   const int npb = (np + 7) & ~7;  // block Jacobi pads to whole 4-column block pairs
@@ -173,10 +175,11 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
     a.alpha = alpha;
     a.ctr_in = cin;
     a.ctr_out = cout;
-    a.wrot = Bst;  // written last, over the dead inverse-iteration bands
+    a.wrot = Bst;  // written last, over the solve's dead scratch area
     a.ldr = np;
     a.max_sweeps = max_sweeps;
-    tri_eig_shrink<TRI_NB, 8>(a, A, ld, nrows, smax > 0.f ? (double)smax : 1.0, smem + REG_A);
+    a.row_mass = s_mass;
+    tri_eig_shrink<TRI_NB, 4, 32>(a, A, ld, nrows, smax > 0.f ? (double)smax : 1.0, smem + REG_A);
   } else {
   float* nrm = reinterpret_cast<float*>(sc);
   double* lam = reinterpret_cast<double*>(sc + BMAX_L * 4);
@@ -203,6 +206,7 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
   a.wrot = Bst;
   a.ldr = np;
   a.max_sweeps = max_sweeps;
+  a.row_mass = s_mass;
   __syncthreads();
   eig_finish<float>(a, A, ld, nrows, np, sweeps, capped, smax > 0.f ? (double)smax : 1.0, lam,
                     mu, mup, scl, ord, rrank);
@@ -210,8 +214,15 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
   __syncthreads();
 
   // ---- rotate: out[r][c] = sum_i W[r][i] B[i][c], column chunks staged in A ----
+  // Thread tid computes rows r = tid / RCH + (BT / RCH) k of column c = tid % RCH
+  // in every chunk and keeps their sums of squares.
+  constexpr int RK = BMAX_L / 2 * RCH / BT;  // row slots per thread
+  static_assert(BT % RCH == 0 && RCH % 32 == 0, "rotate layout");
   const int nout = S.ell - 1;
   float* W = Bst;
+  float rss[RK];
+#pragma unroll
+  for (int k = 0; k < RK; ++k) rss[k] = 0.f;
   for (long long c0 = 0; c0 < d; c0 += RCH) {
     __syncthreads();
     for (int idx = tid; idx < nrows * RCH; idx += BT) {
@@ -219,18 +230,53 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
       A[r * RCH + c] = (c0 + c < d) ? buf[(long long)r * ldb + c0 + c] : 0.f;
     }
     __syncthreads();
-    for (int idx = tid; idx < nout * RCH; idx += BT) {
-      const int r = idx / RCH, c = idx % RCH;
-      float s0 = 0.f, s1 = 0.f;
-      const float* wr = W + r * np;
-      int i = 0;
-      for (; i + 1 < nrows; i += 2) {
-        s0 = fmaf(wr[i], A[i * RCH + c], s0);
-        s1 = fmaf(wr[i + 1], A[(i + 1) * RCH + c], s1);
+#pragma unroll
+    for (int k = 0; k < RK; ++k) {
+      const int idx = tid + k * BT;
+      if (idx < nout * RCH) {
+        const int r = idx / RCH, c = idx % RCH;
+        float s0 = 0.f, s1 = 0.f;
+        const float* wr = W + r * np;
+        int i = 0;
+        for (; i + 1 < nrows; i += 2) {
+          s0 = fmaf(wr[i], A[i * RCH + c], s0);
+          s1 = fmaf(wr[i + 1], A[(i + 1) * RCH + c], s1);
+        }
+        if (i < nrows) s0 = fmaf(wr[i], A[i * RCH + c], s0);
+        if (c0 + c < d) {
+          const float v = s0 + s1;
+          out[(long long)r * ldo + c0 + c] = v;
+          rss[k] = fmaf(v, v, rss[k]);
+        }
       }
-      if (i < nrows) s0 = fmaf(wr[i], A[i * RCH + c], s0);
-      if (c0 + c < d) out[(long long)r * ldo + c0 + c] = s0 + s1;
     }
+  }
+  // A row of S'V^T has norm sigma' exactly (Alg. 1): rescale each output row
+  // to its FP64 target sigma'^2. This removes the error that the ratio
+  // sigma'^2 / sigma^2 would otherwise amplify (large for SS merges into a
+  // small direction). Row sums are combined in a fixed order.
+  {
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < RK; ++k) {
+      const float v = warp_sum(rss[k]);
+      if (lane == 0) s_rsum[warp][k] = v;
+    }
+  }
+  __syncthreads();
+  float* rscale = reinterpret_cast<float*>(A);  // staging area is dead now
+  for (int r = tid; r < nout; r += BT) {
+    const int q = r % (BT / RCH), k = r / (BT / RCH);
+    constexpr int WPR = RCH / 32;  // warps per row group
+    float tot = 0.f;
+    for (int w = 0; w < WPR; ++w) tot += s_rsum[q * WPR + w][k];
+    rscale[r] = (tot > 0.f) ? (float)sqrt(s_mass[r] / (double)tot) : 1.f;
+  }
+  __syncthreads();
+  for (long long idx = tid; idx < (long long)nout * d; idx += BT) {
+    const int r = (int)(idx / d);
+    const long long c = idx - (long long)r * d;
+    out[(long long)r * ldo + c] *= rscale[r];
   }
   __syncthreads();
 }

@@ -259,6 +259,12 @@ __device__ void eig_finish(const EigArgs& a, const T* Wm, int ld, int n, int np,
       }
     }
   }
+  if (a.row_mass)
+    for (int k = tid; k < np; k += blockDim.x) {
+      const int r = rrank[k];
+      if (r >= 0 && r < nout) a.row_mass[r] = mup[k];
+      if (k < nout && k >= s_count) a.row_mass[k] = 0.0;
+    }
   for (int k = warp; k < np; k += nwarps) {
     const int r = rrank[k];
     if (r < 0 || r >= nout) continue;

@@ -49,6 +49,7 @@ struct EigArgs {
   int max_sweeps;
   double tol;          // rotate when |gamma| > tol * sqrt(alpha * beta)
   int use_tri;         // 1: tridiagonal eigensolve where it applies (FP32)
+  double* row_mass;    // optional: sigma'^2 of each output row r (ell-1 entries)
 };
 
 // --- launchers (fd_simt.cu) -------------------------------------------------

@@ -112,7 +112,7 @@ __device__ int jacobi_sweeps_f32(float* Wm, int ld, int np, float* nrm, int max_
             const float hyp = sqrtf(fmaf(num, num, den * den));
             float t = __fdividef(fabsf(den), fabsf(num) + hyp);
             if ((num < 0.f) != (den < 0.f)) t = -t;
-            const float cs = rsqrtf(fmaf(t, t, 1.f));
+            const float cs = 1.f / sqrtf(fmaf(t, t, 1.f));  // correctly rounded: cs^2 + sn^2 = 1 unbiased
             const float sn = cs * t;
 #pragma unroll
             for (int c = 0; c < MAXV; ++c) {
@@ -226,7 +226,7 @@ __device__ __forceinline__ void rotate_set(BlockCols<GS, MAXV, NC>& b, float tol
     float t = __fdividef(fabsf(den), fabsf(num) + hyp);
     if ((num < 0.f) != (den < 0.f)) t = -t;
     t = doit ? t : 0.f;
-    cs[i] = rsqrtf(fmaf(t, t, 1.f));
+    cs[i] = 1.f / sqrtf(fmaf(t, t, 1.f));  // correctly rounded: cs^2 + sn^2 = 1 unbiased
     sn[i] = cs[i] * t;
     const float na = fmaf(-t, ga, al), nb = fmaf(t, ga, be);
     recompute |= doit && (na < 0.25f * al || nb < 0.25f * be);

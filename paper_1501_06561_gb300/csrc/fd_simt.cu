@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(NT) eig_fast_kernel(EigArgs a) {
 
 // Full-buffer FP32 reductions: Householder tridiagonalisation, bisection and
 // inverse iteration (fd_tridiag.cuh), G scaled by its largest diagonal entry.
-template <int NB, int VPW>
+template <int NB, int R, int MAXJ>
 __global__ void __launch_bounds__(512) eig_tri_kernel(EigArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = a.n;
@@ -334,29 +334,32 @@ __global__ void __launch_bounds__(512) eig_tri_kernel(EigArgs a) {
   const float inv = (smax > 0.f) ? 1.f / smax : 1.f;
   for (int idx = tid; idx < n * ld; idx += blockDim.x) A[idx] *= inv;
   __syncthreads();
-  tri_eig_shrink<NB, VPW>(a, A, ld, n, (smax > 0.f) ? (double)smax : 1.0,
-                          smem_raw + tri_al16((size_t)n * ld * 4));
+  tri_eig_shrink<NB, R, MAXJ>(a, A, ld, n, (smax > 0.f) ? (double)smax : 1.0,
+                              smem_raw + tri_al16((size_t)n * ld * 4));
 }
 
-template <int NB, int VPW>
+template <int NB, int R, int MAXJ>
 cudaError_t launch_tri(const EigArgs& a, size_t smem, cudaStream_t st) {
   static size_t attr_set = 0;
   if (smem > attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(eig_tri_kernel<NB, VPW>,
+    cudaError_t e = cudaFuncSetAttribute(eig_tri_kernel<NB, R, MAXJ>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = smem;
   }
-  eig_tri_kernel<NB, VPW><<<1, 512, smem, st>>>(a);
+  eig_tri_kernel<NB, R, MAXJ><<<1, 512, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-// Whether a reduction of n rows takes the tridiagonal eigensolve (full
-// buffers of at most 206 rows; flushes of a partial buffer keep Jacobi).
+// Whether a reduction of n rows takes the tridiagonal eigensolve: full
+// buffers whose solve fits in shared memory (n <= 206); flushes of a partial
+// buffer keep Jacobi. 1: n <= 128, 2 and 3: up to 208 rows (LU batches of
+// 16 or 8 vectors for the fallback path).
 int tri_config(int n, int ell) {
   if (n != 2 * ell || n < 4) return 0;
   if (n <= 128 && tri_smem_bytes(n, 32) <= 226 * 1024) return 1;
-  if (tri_smem_bytes(n, 16) <= 226 * 1024) return 2;
+  if (n <= 208 && tri_smem_bytes(n, 16) <= 226 * 1024) return 2;
+  if (n <= 208 && tri_smem_bytes(n, 8) <= 226 * 1024) return 3;
   return 0;
 }
 
@@ -390,8 +393,9 @@ cudaError_t launch_eig_shrink(const EigArgs& a, cudaStream_t st) {
   const int np = a.n + (a.n & 1);
   if (sizeof(T) == 4 && a.work == nullptr && a.use_tri) {
     const int cfg = tri_config(a.n, a.ell);
-    if (cfg == 1) return launch_tri<32, 4>(a, tri_smem_bytes(a.n, 32), st);
-    if (cfg == 2) return launch_tri<16, 8>(a, tri_smem_bytes(a.n, 16), st);
+    if (cfg == 1) return launch_tri<32, 8, 16>(a, tri_smem_bytes(a.n, 32), st);
+    if (cfg == 2) return launch_tri<16, 4, 52>(a, tri_smem_bytes(a.n, 16), st);
+    if (cfg == 3) return launch_tri<8, 4, 52>(a, tri_smem_bytes(a.n, 8), st);
   }
   if (sizeof(T) == 4 && a.work == nullptr && np <= 224 && eig_fast_smem(np) <= 226 * 1024) {
     const size_t smem = eig_fast_smem(np);

@@ -1,24 +1,37 @@
-// Symmetric eigensolve of the 2*ell x 2*ell Gram by Householder reduction to
-// tridiagonal form, bisection for the eigenvalues and inverse iteration for
-// the eigenvectors that the ReduceRank step keeps (FP32, one CTA, shared
-// memory). It replaces the Jacobi sweeps for full-buffer reductions: about
-// (4/3) n^3 + n^2 * (kept vectors) operations instead of ~25 n^3.
+// Symmetric eigensolve of the n x n buffer Gram (n = 2*ell, a full buffer) in
+// FP32 on one CTA, for the ReduceRank step of Sec. 2.3. Only the retained
+// directions need eigenvectors, so the solve is split:
 //
-//   1. A = Q T Q^T: n-2 Householder steps. Step k reflects the trailing
-//      column with v_k (unit, length n-k-1) and updates the trailing block by
-//      the rank-2 correction A22 -= v q^T + q v^T, q = 2 (A22 v - (v^T A22 v) v).
-//      v_k is kept in A's strictly lower part (column k below the diagonal).
-//   2. Eigenvalues of T by bisection on Sturm counts, one thread per
-//      eigenvalue, sorted descending by construction.
-//   3. After ReduceRank decides which positions are kept, one eigenvector of
-//      T per kept position by inverse iteration: (T - lambda I) z = z solved by
-//      LU with partial pivoting, three times. Vectors are then made
-//      orthonormal (classical Gram-Schmidt, twice) and mapped back, u = Q z.
+//   1. Householder reduction T = Q^T G Q (n-2 reflectors). Step s computes
+//      p = A22 v, K = v^T p, q = 2 (p - K v) and A22 <- A22 - v q^T - q v^T.
+//      The update of step s and the product A33 v_{s+1} of step s+1 share one
+//      pass over the trailing block (the next reflector is formed from the
+//      updated column first), so each step costs one read and one write of
+//      the trailing block and two barriers. Reflector vectors are packed, in
+//      step order, into the finished leading rows of the same buffer.
+//   2. All eigenvalues of T from Sturm counts of T - x I (LDL^T pivots):
+//      one count per thread on an even grid brackets every eigenvalue, then
+//      groups of lanes refine each bracket by multisection. Values at or
+//      below the bisection's resolution, 2 eps lambda_1, count as zero.
+//   3. For each retained position r, an eigenvector of T from a twisted
+//      factorisation of T - lambda_r I (forward and backward LDL^T pivots,
+//      twist index at the smallest |gamma|): one thread per vector, O(n).
+//   4. One Cholesky-QR pass (C = Z^T Z = L L^T, Z <- Z L^-T) makes the
+//      vectors orthonormal. If a twisted vector fails or C has a pivot
+//      below 1/4 (vectors too close to dependent, e.g. a multiple
+//      eigenvalue), every vector is recomputed by inverse iteration from a
+//      random start (pivoted LU, three solves) and orthonormalised by
+//      classical Gram-Schmidt twice.
+//   5. u_r = Q z_r = H_0 ... H_{n-3} z_r with each thread holding a strided
+//      slice of one vector in registers; the rotate matrix rows
+//      sqrt(mu'_r / mu_r) u_r go straight to their destination.
 //
-// Storage: A is n x ld (ld >= n). After step 1 its strictly upper part is
-// free; kept vector c (0 <= c <= n/2-2) lives there, split over two row tails
-// of total length n: entries [0, n-1-c) in row c (columns c+1..n-1) and the
-// rest in row n-2-c (columns n-1-c..n-1).
+// Memory: A (n x ld floats, ld >= n) holds G on entry; afterwards its front
+// holds the packed reflectors (n(n-1)/2 floats) and, from tri_zoff(n), the
+// eigenvector block Zt (n x ldz, column r = vector r). The `rest` region
+// holds a scratch area first (LU bands, the Cholesky matrix, bisection
+// counts; dead when the rotate matrix is written, so a caller may point the
+// rotate output at it), then the spectra and small vectors.
 #pragma once
 
 #include "fd_eig.cuh"
@@ -26,98 +39,208 @@
 
 namespace fdk {
 
-__device__ __forceinline__ float tri_block_sum(float v, float* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  float s = 0.f;
-  for (int w = 0; w < nw; ++w) s += red[w];
-  return s;
+constexpr int TRI_MAXN = 256;
+constexpr int TRI_MAXT = TRI_MAXN / 32;  // column chunks per lane in step 1
+constexpr int TRI_KR = 16;               // row slots per warp in step 1 (n - 1 <= 16 * warps)
+
+__host__ __device__ constexpr size_t tri_al16(size_t b) { return (b + 15) / 16 * 16; }
+// offset (floats) of reflector s (length n-1-s) in the packed store
+__host__ __device__ constexpr int tri_voff(int n, int s) { return s * (n - 1) - (s * (s - 1)) / 2; }
+// offset (floats) of the eigenvector block inside the A region
+__host__ __device__ constexpr int tri_zoff(int n) { return (n * (n - 1) / 2 + 3) & ~3; }
+__host__ __device__ constexpr int tri_ldz(int count) { return count | 1; }
+
+// rest-region pieces (bytes)
+__host__ __device__ constexpr size_t tri_scratch_bytes(int n, int NB) {
+  // max of: LU bands + pivots (NB vectors), Cholesky matrix + inverse diagonal
+  // (count <= n/2), Sturm counts of the grid pass (<= 1024 threads)
+  return (tri_al16((size_t)NB * n * 16) + tri_al16((size_t)NB * n)) >
+                 tri_al16((size_t)(n / 2) * ((n / 2) | 1) * 4) + tri_al16((size_t)(n / 2) * 4) + 4096
+             ? tri_al16((size_t)NB * n * 16) + tri_al16((size_t)NB * n)
+             : tri_al16((size_t)(n / 2) * ((n / 2) | 1) * 4) + tri_al16((size_t)(n / 2) * 4) + 4096;
+}
+__host__ __device__ constexpr size_t tri_rest_bytes(int n, int NB) {
+  return tri_scratch_bytes(n, NB) + tri_al16((size_t)n * 16)  // mu, mup
+         + tri_al16((size_t)(9 * n + 64) * 4)                 // d e e2 lam xb vb0 vb1 qb pb, red
+         + tri_al16((size_t)(2 * n + 16) * 4);                // rrank pos
+}
+// Shared-memory bytes of the whole solve for n rows (A with stride n | 1).
+__host__ __device__ constexpr size_t tri_smem_bytes(int n, int NB) {
+  return tri_al16((size_t)n * (size_t)(n | 1) * 4) + tri_rest_bytes(n, NB);
 }
 
-// Address of entry i of kept vector c in the split layout.
-__device__ __forceinline__ float* zslot(float* A, int ld, int n, int c, int i) {
-  return (i < n - 1 - c) ? (A + (size_t)c * ld + (c + 1 + i)) : (A + (size_t)(n - 2 - c) * ld + i);
-}
-
-// Step 1. d (n) and e (n-1) receive the tridiagonal; vb, pb: n floats.
-static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, float* vb, float* pb,
-                           float* red) {
+// ---------------------------------------------------------------------------
+// Step 1. d (n) and e (n-1) receive T; xb, vb0, vb1, qb, pb: n floats each;
+// red: 64 floats.
+// ---------------------------------------------------------------------------
+static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, float* xb,
+                                  float* vb0, float* vb1, float* qb, float* pb, float* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
-  for (int k = 0; k + 2 < n; ++k) {
-    const int m = n - k - 1;
-    float* colk = A + (size_t)(k + 1) * ld + k;  // colk[i * ld] = A[k+1+i][k]
-    float s = 0.f;
-    for (int i = tid; i < m; i += nt) {
-      const float x = colk[(size_t)i * ld];
-      s = fmaf(x, x, s);
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  float* kpart = red;       // per-warp parts of K = v^T p
+  float* npart = red + 32;  // per-warp parts of ||x||^2
+  if (tid == 0) d[0] = A[0];
+  {
+    float sq = 0.f;
+    for (int i = tid; i < n - 1; i += nt) {
+      const float x = A[(size_t)(i + 1) * ld];
+      xb[i] = x;
+      sq = fmaf(x, x, sq);
     }
-    const float ss = tri_block_sum(s, red);
-    const float x0 = colk[0];
-    float alpha = 0.f, scale = 0.f;
-    if (ss > 0.f) {
+    sq = warp_sum(sq);
+    if (lane == 0) npart[warp] = sq;
+  }
+  __syncthreads();
+  for (int s = 0; s + 1 < n; ++s) {
+    const int m = n - 1 - s;  // length of x_s = size of the trailing block
+    float* vcur = (s & 1) ? vb1 : vb0;
+    const float* vprv = (s & 1) ? vb0 : vb1;
+    // reflector s: v = (x - alpha e_1) / ||x - alpha e_1||, alpha = -sign(x_0) ||x||
+    float ss = 0.f;
+    for (int w = 0; w < nw; ++w) ss += npart[w];
+    const float x0 = xb[0];
+    float alpha = x0, scale = 0.f;  // a length-1 (or zero) column needs no reflection
+    if (m > 1 && ss > 0.f) {
       const float nx = sqrtf(ss);
       alpha = (x0 >= 0.f) ? -nx : nx;
-      scale = rsqrtf(2.f * (ss - x0 * alpha));  // 1 / ||x - alpha e_1||
+      scale = 1.f / sqrtf(2.f * (ss - x0 * alpha));
     }
-    for (int i = tid; i < m; i += nt)
-      vb[i] = ((i == 0) ? (x0 - alpha) : colk[(size_t)i * ld]) * scale;
-    if (tid == 0) {
-      d[k] = A[(size_t)k * ld + k];
-      e[k] = alpha;
-    }
-    __syncthreads();
-    // p = A22 v, one thread per row (rows are ld apart: conflict-free for odd ld)
-    const float* A22 = A + (size_t)(k + 1) * ld + (k + 1);
-    for (int i = tid; i < m; i += nt) {
-      const float* row = A22 + (size_t)i * ld;
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      int j = 0;
-      for (; j + 3 < m; j += 4) {
-        a0 = fmaf(row[j], vb[j], a0);
-        a1 = fmaf(row[j + 1], vb[j + 1], a1);
-        a2 = fmaf(row[j + 2], vb[j + 2], a2);
-        a3 = fmaf(row[j + 3], vb[j + 3], a3);
+    if (tid == 0) e[s] = alpha;
+    if (m > 1) {
+      float* vpk = A + tri_voff(n, s);  // inside rows 0..s, which are finished
+      for (int i = tid; i < m; i += nt) {
+        const float v = ((i == 0) ? (x0 - alpha) : xb[i]) * scale;
+        vcur[i] = v;
+        vpk[i] = v;
       }
-      for (; j < m; ++j) a0 = fmaf(row[j], vb[j], a0);
-      pb[i] = (a0 + a1) + (a2 + a3);
+    }
+    // trailing block rows/cols s+1..n-1: apply step s-1 (vprv, qb at offset
+    // +1) and accumulate p_s = A v_s. Warp w takes rows r = w + k nw
+    // (k < TRI_KR) with its lanes along each row; the row sums of all lanes
+    // are combined at the end by one butterfly over the TRI_KR row slots.
+    {
+      const bool upd = s > 0;
+      const int tmax = (m + 31) >> 5;
+      float wc[TRI_MAXT], vc[TRI_MAXT], qc[TRI_MAXT];
+#pragma unroll
+      for (int t = 0; t < TRI_MAXT; ++t) {
+        const int c = lane + 32 * t;
+        wc[t] = vc[t] = qc[t] = 0.f;
+        if (c < m) {
+          wc[t] = ((c == 0) ? (x0 - alpha) : xb[c]) * scale;
+          if (upd) {
+            vc[t] = vprv[c + 1];
+            qc[t] = qb[c + 1];
+          }
+        }
+      }
+      float acc[TRI_KR];
+#pragma unroll
+      for (int k = 0; k < TRI_KR; ++k) acc[k] = 0.f;
+#pragma unroll
+      for (int k0 = 0; k0 < TRI_KR; k0 += 4) {
+        if (warp + k0 * nw < m) {  // uniform across the warp
+#pragma unroll
+          for (int k = k0; k < k0 + 4; ++k) {
+            const int r = warp + k * nw;
+            const bool rv = r < m;
+            const int rr = rv ? r : m - 1;
+            float* row = A + (size_t)(s + 1 + rr) * ld + (s + 1);
+            const float vr = (upd && rv) ? vprv[rr + 1] : 0.f;
+            const float qr = (upd && rv) ? qb[rr + 1] : 0.f;
+#pragma unroll
+            for (int t = 0; t < TRI_MAXT; ++t) {
+              if (t < tmax) {
+                const int c = lane + 32 * t;
+                if (c < m) {
+                  float a = row[c];
+                  if (upd) {
+                    a = fmaf(-vr, qc[t], fmaf(-qr, vc[t], a));
+                    if (rv) row[c] = a;
+                  }
+                  acc[k] = fmaf(a, wc[t], acc[k]);
+                }
+              }
+            }
+          }
+        }
+      }
+      // butterfly over the 16 slots: lane l ends with slot (l >> 1) summed over all lanes
+      const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+      float l1[8], l2[4], l3[2];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        l1[q] = (b4 ? acc[8 + q] : acc[q]) + __shfl_xor_sync(0xffffffffu, b4 ? acc[q] : acc[8 + q], 16);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        l2[q] = (b3 ? l1[4 + q] : l1[q]) + __shfl_xor_sync(0xffffffffu, b3 ? l1[q] : l1[4 + q], 8);
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        l3[q] = (b2 ? l2[2 + q] : l2[q]) + __shfl_xor_sync(0xffffffffu, b2 ? l2[q] : l2[2 + q], 4);
+      float tot = (b1 ? l3[1] : l3[0]) + __shfl_xor_sync(0xffffffffu, b1 ? l3[0] : l3[1], 2);
+      tot += __shfl_xor_sync(0xffffffffu, tot, 1);
+      const int r = warp + (lane >> 1) * nw;
+      float kp = 0.f;
+      if (!(lane & 1) && r < m) {
+        pb[r] = tot;
+        kp = ((r == 0) ? (x0 - alpha) : xb[r]) * scale * tot;
+      }
+      kp = warp_sum(kp);
+      if (lane == 0) kpart[warp] = kp;
     }
     __syncthreads();
-    float kp = 0.f;
-    for (int i = tid; i < m; i += nt) kp = fmaf(vb[i], pb[i], kp);
-    const float K = tri_block_sum(kp, red);
-    for (int i = tid; i < m; i += nt) pb[i] = 2.f * fmaf(-K, vb[i], pb[i]);
-    __syncthreads();
-    // A22 -= v q^T + q v^T (one warp per row); keep v in column k
-    for (int i = warp; i < m; i += nwarps) {
-      float* row = A + (size_t)(k + 1 + i) * ld + (k + 1);
-      const float vi = vb[i], qi = pb[i];
-      for (int j = lane; j < m; j += 32) row[j] = fmaf(-vi, pb[j], fmaf(-qi, vb[j], row[j]));
+    if (m == 1) break;
+    // q_s, and column s+1 updated by step s: its diagonal is d[s+1], the
+    // rest is x_{s+1}
+    {
+      float K = 0.f;
+      for (int w = 0; w < nw; ++w) K += kpart[w];
+      const float v0 = vcur[0];
+      const float q0 = 2.f * fmaf(-K, v0, pb[0]);
+      float sq = 0.f;
+      for (int i = tid; i < m; i += nt) {
+        const float vi = vcur[i];
+        const float qi = 2.f * fmaf(-K, vi, pb[i]);
+        qb[i] = qi;
+        float a = A[(size_t)(s + 1 + i) * ld + (s + 1)];
+        a = fmaf(-vi, q0, fmaf(-qi, v0, a));
+        if (i == 0) {
+          d[s + 1] = a;
+        } else {
+          xb[i - 1] = a;
+          sq = fmaf(a, a, sq);
+        }
+      }
+      sq = warp_sum(sq);
+      if (lane == 0) npart[warp] = sq;
     }
-    for (int i = tid; i < m; i += nt) colk[(size_t)i * ld] = vb[i];
     __syncthreads();
   }
-  if (tid == 0) {
-    if (n >= 2) {
-      d[n - 2] = A[(size_t)(n - 2) * ld + (n - 2)];
-      e[n - 2] = A[(size_t)(n - 1) * ld + (n - 2)];
-    }
-    d[n - 1] = A[(size_t)(n - 1) * ld + (n - 1)];
-  }
+  if (tid == 0) d[n - 1] = A[(size_t)(n - 1) * ld + (n - 1)];
   __syncthreads();
 }
 
-// Number of eigenvalues of T below x (Sturm sequence of the LDL^T pivots).
+// Number of eigenvalues of T below x (signs of the LDL^T pivots of T - x I).
 __device__ __forceinline__ int tri_sturm(const float* d, const float* e2, int n, float x,
                                          float pivmin) {
   float q = d[0] - x;
   int cnt = (q < 0.f);
-  for (int i = 1; i < n; ++i) {
+  int i = 1;
+  for (; i + 7 < n; i += 8) {  // loads of a chunk first, then the pivot chain
+    float dx[8], ee[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      dx[u] = d[i + u] - x;
+      ee[u] = e2[i - 1 + u];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (fabsf(q) < pivmin) q = -pivmin;
+      q = dx[u] - __fdividef(ee[u], q);
+      cnt += (q < 0.f);
+    }
+  }
+  for (; i < n; ++i) {
     if (fabsf(q) < pivmin) q = -pivmin;
     q = (d[i] - x) - __fdividef(e2[i - 1], q);
     cnt += (q < 0.f);
@@ -125,10 +248,12 @@ __device__ __forceinline__ int tri_sturm(const float* d, const float* e2, int n,
   return cnt;
 }
 
-// Step 2. lam[j] = j-th largest eigenvalue of T (one thread per eigenvalue).
-// Returns the Gershgorin bound of ||T|| through *tnorm_out (shared).
+// ---------------------------------------------------------------------------
+// Step 2. lam[j] = j-th largest eigenvalue of T. cnt: blockDim.x ints of
+// scratch. Returns the Gershgorin bound of ||T|| through *tnorm_out (shared).
+// ---------------------------------------------------------------------------
 static __device__ void tri_bisect(const float* d, const float* e, float* e2, int n, float* lam,
-                           float* tnorm_out) {
+                                  float* tnorm_out, int* cnt) {
   const int tid = threadIdx.x, nt = blockDim.x;
   __shared__ float s_lo, s_hi;
   for (int i = tid; i < n - 1; i += nt) e2[i] = e[i] * e[i];
@@ -144,29 +269,295 @@ static __device__ void tri_bisect(const float* d, const float* e, float* e2, int
     *tnorm_out = fmaxf(fabsf(lo), fabsf(hi));
   }
   __syncthreads();
-  const float tnorm = fmaxf(fabsf(s_lo), fabsf(s_hi));
+  const float glo = s_lo, ghi = s_hi;
+  const float tnorm = fmaxf(fabsf(glo), fabsf(ghi));
   const float eps = 1.1920929e-07f;
   const float pivmin = fmaxf(tnorm, 1e-30f) * 1e-30f;
   const float atol = 2.f * eps * tnorm;
-  const float span = s_hi - s_lo;
-  for (int j = tid; j < n; j += nt) {
-    const int target = n - 1 - j;  // 0-based index from the smallest
-    float lo = s_lo - 0.01f * span - atol, hi = s_hi + 0.01f * span + atol;
-    for (int it = 0; it < 80; ++it) {
-      if (hi - lo <= atol + 2.f * eps * fmaxf(fabsf(lo), fabsf(hi))) break;
-      const float mid = 0.5f * (lo + hi);
-      if (tri_sturm(d, e2, n, mid, pivmin) > target) hi = mid; else lo = mid;
+  const float lo0 = glo - 0.01f * (ghi - glo) - atol;
+  const float hi0 = ghi + 0.01f * (ghi - glo) + atol;
+  const float h = (hi0 - lo0) / (float)(nt + 1);
+  // grid pass: counts at lo0 + (p + 1) h, p = 0..nt-1 (non-decreasing in p)
+  cnt[tid] = tri_sturm(d, e2, n, lo0 + (float)(tid + 1) * h, pivmin);
+  __syncthreads();
+  int G = 1;  // lanes per eigenvalue (power of two, <= 8)
+  while (G < 8 && 2 * G * n <= nt) G <<= 1;
+  const int sub = tid & (G - 1);
+  const int per = nt / G;
+  for (int j0 = 0; j0 < n; j0 += per) {
+    const int j = j0 + tid / G;
+    const bool act = j < n;
+    const int target = n - 1 - j;  // lambda_j is the target-th smallest (0-based)
+    float lo = lo0, hi = hi0;
+    if (act) {
+      int a = -1, b = nt;  // count(x_a) <= target < count(x_b)
+      while (b - a > 1) {
+        const int mid = (a + b) >> 1;
+        if (cnt[mid] <= target) a = mid; else b = mid;
+      }
+      if (a >= 0) lo = lo0 + (float)(a + 1) * h;
+      if (b < nt) hi = lo0 + (float)(b + 1) * h;
     }
-    lam[j] = 0.5f * (lo + hi);
+    for (int it = 0; it < 64; ++it) {
+      const bool done = !act || (hi - lo <= atol + 2.f * eps * fmaxf(fabsf(lo), fabsf(hi)));
+      if (__all_sync(0xffffffffu, done)) break;
+      const float x = lo + (hi - lo) * (float)(sub + 1) / (float)(G + 1);
+      const int c = act ? tri_sturm(d, e2, n, x, pivmin) : 0;
+      float nlo = (c <= target) ? x : lo;
+      float nhi = (c > target) ? x : hi;
+      for (int o = 1; o < G; o <<= 1) {
+        nlo = fmaxf(nlo, __shfl_xor_sync(0xffffffffu, nlo, o));
+        nhi = fminf(nhi, __shfl_xor_sync(0xffffffffu, nhi, o));
+      }
+      if (!done) {
+        lo = nlo;
+        hi = nhi;
+      }
+    }
+    if (act && sub == 0) lam[j] = 0.5f * (lo + hi);
   }
   __syncthreads();
 }
 
-// Step 3a. Inverse iteration for kept vectors c = c0 + t (t < NB, c < cend):
-// eigenvalue lam[pos[c]]; the vector is written to its slot. Scratch holds
-// NB interleaved copies of the four LU bands plus NB x n pivot bytes.
+// ---------------------------------------------------------------------------
+// Step 3. Eigenvector of T for eigenvalue lmb from the twisted factorisation
+// of T - lmb I (one thread). z: n entries with stride ldz. Returns false if
+// the vector came out zero or not finite.
+//   forward pivots  D+_0 = d_0 - lmb,     D+_i = d_i - lmb - e_{i-1}^2 / D+_{i-1}
+//   backward pivots D-_{n-1} = d_{n-1} - lmb, D-_i = d_i - lmb - e_i^2 / D-_{i+1}
+//   gamma_r = D+_r - e_r^2 / D-_{r+1};  z_r = 1,
+//   z_i = -e_i z_{i+1} / D+_i (i < r),  z_{i+1} = -e_i z_i / D-_{i+1} (i >= r)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float tri_clamp_piv(float q, float pivmin) {
+  return (fabsf(q) < pivmin) ? -pivmin : q;
+}
+
+static __device__ bool tri_twisted(const float* d, const float* e, const float* e2, int n,
+                                   float lmb, float pivmin, float* z, int ldz) {
+  // (each pass loads a chunk of 8 entries ahead of its recurrence)
+  float dp = tri_clamp_piv(d[0] - lmb, pivmin);
+  z[0] = dp;
+  int i = 1;
+  for (; i + 7 < n; i += 8) {
+    float dx[8], ee[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      dx[u] = d[i + u] - lmb;
+      ee[u] = e2[i - 1 + u];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      dp = tri_clamp_piv(dx[u] - __fdividef(ee[u], dp), pivmin);
+      z[(size_t)(i + u) * ldz] = dp;
+    }
+  }
+  for (; i < n; ++i) {
+    dp = tri_clamp_piv((d[i] - lmb) - __fdividef(e2[i - 1], dp), pivmin);
+    z[(size_t)i * ldz] = dp;
+  }
+  float dm = tri_clamp_piv(d[n - 1] - lmb, pivmin);
+  int r = n - 1;
+  float best = fabsf(dp);
+  i = n - 2;
+  for (; i >= 7; i -= 8) {
+    float dx[8], ee[8], zp[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      dx[u] = d[i - u] - lmb;
+      ee[u] = e2[i - u];
+      zp[u] = z[(size_t)(i - u) * ldz];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float q = __fdividef(ee[u], dm);
+      const float g = fabsf(zp[u] - q);
+      if (g < best) {
+        best = g;
+        r = i - u;
+      }
+      dm = tri_clamp_piv(dx[u] - q, pivmin);
+    }
+  }
+  for (; i >= 0; --i) {
+    const float q = __fdividef(e2[i], dm);
+    const float g = fabsf(z[(size_t)i * ldz] - q);
+    if (g < best) {
+      best = g;
+      r = i;
+    }
+    dm = tri_clamp_piv((d[i] - lmb) - q, pivmin);
+  }
+  // D-_i for i > r replace D+_i (no longer needed there)
+  dm = tri_clamp_piv(d[n - 1] - lmb, pivmin);
+  i = n - 1;
+  for (; i - 7 > r; i -= 8) {
+    float dx[8], ee[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      dx[u] = d[i - 1 - u] - lmb;
+      ee[u] = e2[i - 1 - u];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      z[(size_t)(i - u) * ldz] = dm;
+      dm = tri_clamp_piv(dx[u] - __fdividef(ee[u], dm), pivmin);
+    }
+  }
+  for (; i > r; --i) {
+    z[(size_t)i * ldz] = dm;
+    dm = tri_clamp_piv((d[i - 1] - lmb) - __fdividef(e2[i - 1], dm), pivmin);
+  }
+  z[(size_t)r * ldz] = 1.f;
+  float s2 = 1.f, zz = 1.f;
+  i = r - 1;
+  for (; i >= 7; i -= 8) {
+    float ee[8], dd[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      ee[u] = e[i - u];
+      dd[u] = z[(size_t)(i - u) * ldz];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      zz = -__fdividef(ee[u] * zz, dd[u]);
+      z[(size_t)(i - u) * ldz] = zz;
+      s2 = fmaf(zz, zz, s2);
+    }
+  }
+  for (; i >= 0; --i) {
+    zz = -__fdividef(e[i] * zz, z[(size_t)i * ldz]);
+    z[(size_t)i * ldz] = zz;
+    s2 = fmaf(zz, zz, s2);
+  }
+  zz = 1.f;
+  i = r;
+  for (; i + 8 < n; i += 8) {
+    float ee[8], dd[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      ee[u] = e[i + u];
+      dd[u] = z[(size_t)(i + u + 1) * ldz];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      zz = -__fdividef(ee[u] * zz, dd[u]);
+      z[(size_t)(i + u + 1) * ldz] = zz;
+      s2 = fmaf(zz, zz, s2);
+    }
+  }
+  for (; i + 1 < n; ++i) {
+    zz = -__fdividef(e[i] * zz, z[(size_t)(i + 1) * ldz]);
+    z[(size_t)(i + 1) * ldz] = zz;
+    s2 = fmaf(zz, zz, s2);
+  }
+  if (!(s2 < 3.0e38f)) return false;
+  const float inv = rsqrtf(s2);
+  for (int k = 0; k < n; ++k) z[(size_t)k * ldz] *= inv;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Step 4. One Cholesky-QR pass over the columns of Zt (n x count, stride
+// ldz): C = Zt^T Zt = L L^T (C: count x ldc, lower triangle; dinv: count),
+// Zt <- Zt L^-T. Returns false, with Zt unchanged, if a pivot of C is below
+// tau (uniform across the block).
+// ---------------------------------------------------------------------------
+static __device__ bool tri_cholqr(float* Zt, int ldz, int n, int count, float* C, int ldc,
+                                  float* dinv, float tau) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nb = (count + 3) >> 2;
+  const int ntile = nb * (nb + 1) / 2;
+  for (int t = tid; t < ntile; t += nt) {
+    int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    while (ti * (ti + 1) / 2 > t) --ti;
+    const int tj = t - ti * (ti + 1) / 2;
+    const int a0 = 4 * ti, b0 = 4 * tj;
+    float acc[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
+#pragma unroll 4
+    for (int i = 0; i < n; ++i) {
+      const float* zr = Zt + (size_t)i * ldz;
+      float za[4], zb[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        za[q] = (a0 + q < count) ? zr[a0 + q] : 0.f;
+        zb[q] = (b0 + q < count) ? zr[b0 + q] : 0.f;
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(za[p], zb[q], acc[p][q]);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (a0 + p < count && b0 + q <= a0 + p) C[(size_t)(a0 + p) * ldc + b0 + q] = acc[p][q];
+  }
+  __syncthreads();
+  // right-looking Cholesky; the trailing update of column j runs over all
+  // (i, k), j < k <= i < count, flattened across the block
+  for (int j = 0; j < count; ++j) {
+    const float piv = C[(size_t)j * ldc + j];  // not written during step j
+    if (!(piv >= tau)) return false;           // same value in every thread
+    const float rinv = 1.f / sqrtf(piv);
+    for (int i = j + 1 + tid; i < count; i += nt) C[(size_t)i * ldc + j] *= rinv;
+    if (tid == 0) dinv[j] = rinv;
+    __syncthreads();
+    const int mm = count - 1 - j;
+    const int tot = mm * (mm + 1) / 2;
+    for (int t = tid; t < tot; t += nt) {
+      int ii = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+      while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+      while (ii * (ii + 1) / 2 > t) --ii;
+      const int kk = t - ii * (ii + 1) / 2;
+      const int i = j + 1 + ii, k = j + 1 + kk;
+      C[(size_t)i * ldc + k] =
+          fmaf(-C[(size_t)i * ldc + j], C[(size_t)k * ldc + j], C[(size_t)i * ldc + k]);
+    }
+    __syncthreads();
+  }
+  // row i of Zt solves q L^T = z: q_c = (z_c - sum_{b<c} q_b L_cb) / L_cc
+  for (int i = tid; i < n; i += nt) {
+    float* zr = Zt + (size_t)i * ldz;
+    for (int c = 0; c < count; ++c) {
+      const float* Lc = C + (size_t)c * ldc;
+      float a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = 0.f;
+      a[0] = zr[c];
+      int b = 0;
+      for (; b + 7 < c; b += 8) {
+        float zq[8], lq[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          zq[u] = zr[b + u];
+          lq[u] = Lc[b + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = fmaf(-zq[u], lq[u], a[u]);
+      }
+      for (; b < c; ++b) a[0] = fmaf(-zr[b], Lc[b], a[0]);
+      zr[c] = (((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]))) * dinv[c];
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Fallback of steps 3-4: inverse iteration from a random start for vectors
+// c0 .. min(c0+NB, cend)-1 (thread t < NB takes vector c0 + t): eigenvalue
+// lam[pos[c]], (T - lambda I) z = z solved three times by LU with partial
+// pivoting. scr holds NB interleaved copies of the four LU bands, piv NB x n
+// pivot flags.
+// ---------------------------------------------------------------------------
 template <int NB>
-__device__ void tri_invit_batch(float* A, int ld, int n, const float* d, const float* e,
+__device__ void tri_invit_batch(float* Zt, int ldz, int n, const float* d, const float* e,
                                 const float* lam, const int* pos, int c0, int cend, float tnorm,
                                 float* scr, unsigned char* piv) {
   const int t = threadIdx.x;
@@ -176,17 +567,23 @@ __device__ void tri_invit_batch(float* A, int ld, int n, const float* d, const f
   float* du = scr + (size_t)NB * n;
   float* du2 = scr + (size_t)2 * NB * n;
   float* dl = scr + (size_t)3 * NB * n;
+  float* z = Zt + c;
 #define DD(i) dd[(size_t)(i) * NB + t]
 #define DU(i) du[(size_t)(i) * NB + t]
 #define DU2(i) du2[(size_t)(i) * NB + t]
 #define DL(i) dl[(size_t)(i) * NB + t]
 #define PV(i) piv[(size_t)(i) * NB + t]
+#define Z(i) z[(size_t)(i) * ldz]
   const float eps = 1.1920929e-07f;
   const float tiny = eps * fmaxf(tnorm, 1e-30f);
   const float lmb = lam[pos[c]];
   for (int i = 0; i < n; ++i) {
     DD(i) = d[i] - lmb;
-    if (i < n - 1) { DU(i) = e[i]; DL(i) = e[i]; DU2(i) = 0.f; }
+    if (i < n - 1) {
+      DU(i) = e[i];
+      DL(i) = e[i];
+      DU2(i) = 0.f;
+    }
   }
   for (int i = 0; i + 1 < n; ++i) {
     const float di = DD(i), li = DL(i);
@@ -213,175 +610,269 @@ __device__ void tri_invit_batch(float* A, int ld, int n, const float* d, const f
     }
   }
   if (DD(n - 1) == 0.f) DD(n - 1) = tiny;
-  // start vector: ones with a small deterministic perturbation
-  for (int i = 0; i < n; ++i) {
+  for (int i = 0; i < n; ++i) {  // start: ones with a small deterministic perturbation
     unsigned h = (unsigned)(i * 2654435761u) ^ (unsigned)(c * 40503u + 0x9e3779b9u);
     h ^= h >> 15;
     h *= 2246822519u;
     h ^= h >> 13;
-    *zslot(A, ld, n, c, i) = 1.f + 0.25f * ((float)(h & 0xffff) / 65536.f - 0.5f);
+    Z(i) = 1.f + 0.25f * ((float)(h & 0xffff) / 65536.f - 0.5f);
   }
   for (int rep = 0; rep < 3; ++rep) {
-    // forward (row interchanges as recorded)
     for (int i = 0; i + 1 < n; ++i) {
-      float* bi = zslot(A, ld, n, c, i);
-      float* bj = zslot(A, ld, n, c, i + 1);
       if (!PV(i)) {
-        *bj = *bj - DL(i) * *bi;
+        Z(i + 1) = Z(i + 1) - DL(i) * Z(i);
       } else {
-        const float tmp = *bi;
-        *bi = *bj;
-        *bj = tmp - DL(i) * *bi;
+        const float tmp = Z(i);
+        Z(i) = Z(i + 1);
+        Z(i + 1) = tmp - DL(i) * Z(i);
       }
     }
-    // backward
     float x2 = 0.f, x1 = 0.f;  // z[i+2], z[i+1]
     for (int i = n - 1; i >= 0; --i) {
-      float* bi = zslot(A, ld, n, c, i);
-      float v = *bi;
+      float v = Z(i);
       if (i + 1 < n) v -= DU(i) * x1;
       if (i + 2 < n) v -= DU2(i) * x2;
       v /= DD(i);
-      *bi = v;
+      Z(i) = v;
       x2 = x1;
       x1 = v;
     }
-    // normalise (max-norm first to stay in range)
     float mx = 0.f;
-    for (int i = 0; i < n; ++i) mx = fmaxf(mx, fabsf(*zslot(A, ld, n, c, i)));
+    for (int i = 0; i < n; ++i) mx = fmaxf(mx, fabsf(Z(i)));
     const float inv = (mx > 0.f) ? 1.f / mx : 1.f;
     float s2 = 0.f;
     for (int i = 0; i < n; ++i) {
-      float* bi = zslot(A, ld, n, c, i);
-      const float v = *bi * inv;
-      *bi = v;
+      const float v = Z(i) * inv;
+      Z(i) = v;
       s2 = fmaf(v, v, s2);
     }
     const float r = rsqrtf(fmaxf(s2, 1e-30f));
-    for (int i = 0; i < n; ++i) *zslot(A, ld, n, c, i) *= r;
+    for (int i = 0; i < n; ++i) Z(i) *= r;
   }
 #undef DD
 #undef DU
 #undef DU2
 #undef DL
 #undef PV
+#undef Z
 }
 
-// Step 3b. Kept vectors 0..count-1 orthonormal (classical Gram-Schmidt twice).
-static __device__ void tri_orthonormalize(float* A, int ld, int n, int count, float* hbuf, float* red) {
+__device__ __forceinline__ float tri_block_sum(float v, float* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  float s = 0.f;
+  for (int w = 0; w < nw; ++w) s += red[w];
+  return s;
+}
+
+// Fallback of step 4: columns 0..count-1 of Zt orthonormal by classical
+// Gram-Schmidt, twice per column.
+static __device__ void tri_cgs2(float* Zt, int ldz, int n, int count, float* hbuf, float* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   for (int c = 0; c < count; ++c) {
     for (int pass = 0; pass < 2 && c > 0; ++pass) {
-      for (int cp = warp; cp < c; cp += nwarps) {
+      for (int cp = warp; cp < c; cp += nw) {
         float s = 0.f;
-        for (int i = lane; i < n; i += 32) s = fmaf(*zslot(A, ld, n, cp, i), *zslot(A, ld, n, c, i), s);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        for (int i = lane; i < n; i += 32) s = fmaf(Zt[(size_t)i * ldz + cp], Zt[(size_t)i * ldz + c], s);
+        s = warp_sum(s);
         if (lane == 0) hbuf[cp] = s;
       }
       __syncthreads();
       for (int i = tid; i < n; i += nt) {
         float s = 0.f;
-        for (int cp = 0; cp < c; ++cp) s = fmaf(hbuf[cp], *zslot(A, ld, n, cp, i), s);
-        *zslot(A, ld, n, c, i) -= s;
+        for (int cp = 0; cp < c; ++cp) s = fmaf(hbuf[cp], Zt[(size_t)i * ldz + cp], s);
+        Zt[(size_t)i * ldz + c] -= s;
       }
       __syncthreads();
     }
     float s = 0.f;
     for (int i = tid; i < n; i += nt) {
-      const float v = *zslot(A, ld, n, c, i);
+      const float v = Zt[(size_t)i * ldz + c];
       s = fmaf(v, v, s);
     }
     const float ss = tri_block_sum(s, red);
-    const float r = rsqrtf(fmaxf(ss, 1e-30f));
-    for (int i = tid; i < n; i += nt) *zslot(A, ld, n, c, i) *= r;
+    const float r = 1.f / sqrtf(fmaxf(ss, 1e-30f));
+    for (int i = tid; i < n; i += nt) Zt[(size_t)i * ldz + c] *= r;
     __syncthreads();
   }
 }
 
-// Step 3c. u_c = Q z_c = H_0 H_1 ... H_{n-3} z_c for every kept vector; each
-// warp takes its own vectors through all reflectors (no barrier inside).
-template <int VPW>
-__device__ void tri_back_transform(float* A, int ld, int n, int count) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  for (int k = n - 3; k >= 0; --k) {
-    const int m = n - k - 1;
-    const float* colk = A + (size_t)(k + 1) * ld + k;
-    float g[VPW];
-#pragma unroll
-    for (int q = 0; q < VPW; ++q) g[q] = 0.f;
-    for (int i = lane; i < m; i += 32) {
-      const float v = colk[(size_t)i * ld];
-#pragma unroll
-      for (int q = 0; q < VPW; ++q) {
-        const int c = warp + q * nwarps;
-        if (c < count) g[q] = fmaf(v, *zslot(A, ld, n, c, k + 1 + i), g[q]);
-      }
+// ---------------------------------------------------------------------------
+// Step 5. u_c = H_0 H_1 ... H_{n-3} z_c and the rotate-matrix rows
+// sqrt(mu'/mu) u_c. Thread (c, g) = (tid / R, tid % R) holds rows
+// i = n-1-(g + R j), j < MAXJ, of vector c, so that the rows a reflector
+// touches (i > s) are a prefix in j. Reflectors go four at a time: for the
+// block H_{s-3} H_{s-2} H_{s-1} H_s z with a_k = v_{s-k},
+//   h_k = a_k . z,  g_k = h_k - 2 sum_{j<k} g_j (a_k . a_j),  z -= 2 sum_k g_k a_k,
+// the six products a_k . a_j of every block being formed first (mw: 6 per
+// block). Rows count..ell-2 of the output are zero.
+// ---------------------------------------------------------------------------
+template <int R, int MAXJ>
+__device__ void tri_back_write(const EigArgs& a, const float* V, int n, const float* Zt, int ldz,
+                               int count, const double* mu, const double* mup, const int* pos,
+                               float* mw) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int nout = a.ell - 1;
+  float* wr = reinterpret_cast<float*>(a.wrot);
+  const int nblk = (n - 2 + 3) >> 2;  // reflectors 0..n-3, block b tops at n-3-4b
+  for (int w = warp; w < nblk * 6; w += nw) {
+    const int b = w / 6, p = w - 6 * (w / 6);
+    const int k = (p == 0) ? 1 : (p < 3 ? 2 : 3);
+    const int j = (p == 0) ? 0 : (p == 1 ? 0 : (p == 2 ? 1 : p - 3));
+    const int sb = n - 3 - 4 * b;
+    float sum = 0.f;
+    if (sb - k >= 0) {
+      const float* ak = V + tri_voff(n, sb - k) - (sb - k + 1);
+      const float* aj = V + tri_voff(n, sb - j) - (sb - j + 1);
+      for (int i = sb - j + 1 + lane; i < n; i += 32) sum = fmaf(ak[i], aj[i], sum);
     }
+    sum = warp_sum(sum);
+    if (lane == 0) mw[w] = sum;
+  }
+  __syncthreads();
+  const int per = nt / R;
+  for (int cb = 0; cb < count; cb += per) {  // uniform across the block
+    const int c = cb + tid / R, g = tid % R;
+    const bool act = c < count;
+    float z[MAXJ];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+    for (int j = 0; j < MAXJ; ++j) {
+      const int i = n - 1 - (g + R * j);
+      z[j] = (act && i >= 0) ? Zt[(size_t)i * ldz + c] : 0.f;
+    }
+    for (int b = 0; b < nblk; ++b) {
+      const int sb = n - 3 - 4 * b;
+      int je[4];
+      const float* ap[4];
 #pragma unroll
-      for (int q = 0; q < VPW; ++q) g[q] += __shfl_xor_sync(0xffffffffu, g[q], o);
-    for (int i = lane; i < m; i += 32) {
-      const float v2 = 2.f * colk[(size_t)i * ld];
+      for (int k = 0; k < 4; ++k) {
+        const int sk = sb - k;
+        je[k] = (sk >= 0) ? (n - 1 - sk - g + R - 1) / R : 0;  // rows i > sk: j < je[k]
+        const int sc = sk >= 0 ? sk : 0;
+        ap[k] = V + tri_voff(n, sc) - (sc + 1) + (n - 1 - g);  // a_k[i_j] = ap[k][-R j]
+      }
+      const int jmx = max(max(je[0], je[1]), max(je[2], je[3]));
+      float h[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int q = 0; q < VPW; ++q) {
-        const int c = warp + q * nwarps;
-        if (c < count) {
-          float* zp = zslot(A, ld, n, c, k + 1 + i);
-          *zp = fmaf(-v2, g[q], *zp);
+      for (int j0 = 0; j0 < MAXJ; j0 += 4) {
+        if (j0 >= jmx) break;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u;
+          if (j < MAXJ) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float av = (j < je[k]) ? ap[k][-R * j] : 0.f;
+              h[k] = fmaf(av, z[j], h[k]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 1; o < R; o <<= 1)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) h[k] += __shfl_xor_sync(0xffffffffu, h[k], o);
+      const float* m6 = mw + 6 * b;
+      const float g0 = h[0];
+      const float g1 = h[1] - 2.f * g0 * m6[0];
+      const float g2 = h[2] - 2.f * (g0 * m6[1] + g1 * m6[2]);
+      const float g3 = h[3] - 2.f * (g0 * m6[3] + g1 * m6[4] + g2 * m6[5]);
+      const float t[4] = {2.f * g0, 2.f * g1, 2.f * g2, 2.f * g3};
+#pragma unroll
+      for (int j0 = 0; j0 < MAXJ; j0 += 4) {
+        if (j0 >= jmx) break;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u;
+          if (j < MAXJ) {
+            float upd = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float av = (j < je[k]) ? ap[k][-R * j] : 0.f;
+              upd = fmaf(t[k], av, upd);
+            }
+            z[j] -= upd;
+          }
         }
       }
     }
-    __syncwarp();
+    if (act) {
+      const int k = pos[c];
+      const double sc = (mu[k] > 0.0) ? sqrt(mup[k] / mu[k]) : 0.0;
+      if (a.row_mass && g == 0) a.row_mass[c] = mup[k];
+#pragma unroll
+      for (int j = 0; j < MAXJ; ++j) {
+        const int i = n - 1 - (g + R * j);
+        if (i >= 0) {
+          const float val = (float)(sc * (double)z[j]);
+          wr[(size_t)c * a.ldr + i] = val;
+          if (a.wrot_hi) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(val);
+            a.wrot_hi[(size_t)c * a.ldr16 + i] = hi;
+            a.wrot_lo[(size_t)c * a.ldr16 + i] = __float2bfloat16_rn(val - __bfloat162float(hi));
+          }
+        }
+      }
+    }
+  }
+  if (a.row_mass)
+    for (int r = count + tid; r < nout; r += nt) a.row_mass[r] = 0.0;
+  for (int idx = tid; idx < (nout - count) * n; idx += nt) {
+    const int r = count + idx / n, i = idx % n;
+    wr[(size_t)r * a.ldr + i] = 0.f;
+    if (a.wrot_hi) {
+      a.wrot_hi[(size_t)r * a.ldr16 + i] = __float2bfloat16_rn(0.f);
+      a.wrot_lo[(size_t)r * a.ldr16 + i] = __float2bfloat16_rn(0.f);
+    }
   }
   __syncthreads();
 }
 
-// Shared-memory layout after A (bytes, 16-aligned pieces).
-__host__ __device__ constexpr size_t tri_al16(size_t b) { return (b + 15) / 16 * 16; }
-__host__ __device__ constexpr size_t tri_rest_bytes(int n, int NB) {
-  return tri_al16((size_t)NB * n * 16) + tri_al16((size_t)NB * n)  // LU bands, pivots
-         + tri_al16((size_t)n * 4 * 7 + 64 * 4)                    // d e e2 lam vb pb hbuf, red
-         + tri_al16((size_t)n * 16) + tri_al16((size_t)n * 8);       // mu mup, rrank pos
-}
-// Shared-memory bytes the tridiagonal eigensolve needs for n = 2*ell rows
-// with NB vectors per inverse-iteration batch (A has stride n | 1).
-__host__ __device__ constexpr size_t tri_smem_bytes(int n, int NB) {
-  return tri_al16((size_t)n * (size_t)(n | 1) * 4) + tri_rest_bytes(n, NB);
-}
-
-// The whole eigensolve + shrink + rotate-matrix write for a full buffer of
-// n = 2*ell rows whose Gram is already in A (n x ld, scaled by 1/smax).
-template <int NB, int VPW>
+// ---------------------------------------------------------------------------
+// The whole eigensolve + ReduceRank shrink + rotate-matrix write for a full
+// buffer of n = 2*ell rows whose Gram is in A (n x ld, scaled by 1/smax).
+// NB: vectors per fallback inverse-iteration batch; R, MAXJ: step-5 layout
+// (n <= R * MAXJ, R * min(count, nt / R) <= nt).
+// ---------------------------------------------------------------------------
+template <int NB, int R, int MAXJ>
 __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double smax,
                                unsigned char* rest) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  float* scr = reinterpret_cast<float*>(rest);
-  unsigned char* piv = rest + tri_al16((size_t)NB * n * 16);
-  float* fv = reinterpret_cast<float*>(piv + tri_al16((size_t)NB * n));
+  unsigned char* scr_raw = rest;
+  double* mu = reinterpret_cast<double*>(rest + tri_scratch_bytes(n, NB));
+  double* mup = mu + n;
+  float* fv = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(mu) + tri_al16((size_t)n * 16));
   float* d = fv;
   float* e = d + n;
   float* e2 = e + n;
   float* lam = e2 + n;
-  float* vb = lam + n;
-  float* pb = vb + n;
-  float* hbuf = pb + n;
-  float* red = hbuf + n;  // 64 floats
-  double* mu = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(fv) +
-                                         tri_al16((size_t)n * 4 * 7 + 64 * 4));
-  double* mup = mu + n;
-  int* rrank = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(mu) + tri_al16((size_t)n * 16));
+  float* xb = lam + n;
+  float* vb0 = xb + n;
+  float* vb1 = vb0 + n;
+  float* qb = vb1 + n;
+  float* pb = qb + n;
+  float* red = pb + n;  // 64 floats
+  int* rrank = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(fv) +
+                                      tri_al16((size_t)(9 * n + 64) * 4));
   int* pos = rrank + n;
   __shared__ float s_tnorm;
-  __shared__ int s_count;
+  __shared__ int s_count, s_ok;
   __shared__ double s_dsum, s_dlast;
 
-  tri_reduce(A, ld, n, d, e, vb, pb, red);
-  tri_bisect(d, e, e2, n, lam, &s_tnorm);
-  for (int k = tid; k < n; k += nt) mu[k] = fmax((double)lam[k], 0.0) * smax;
+  tri_reduce(A, ld, n, d, e, xb, vb0, vb1, qb, pb, red);
+  tri_bisect(d, e, e2, n, lam, &s_tnorm, reinterpret_cast<int*>(scr_raw));
+  {
+    // eigenvalues at or below the bisection's resolution (2 eps lambda_1)
+    // are zero: their sign and size are rounding noise
+    const float zfloor = 2.f * 1.1920929e-07f * fmaxf(lam[0], 0.f);
+    for (int k = tid; k < n; k += nt) mu[k] = (lam[k] > zfloor) ? (double)lam[k] * smax : 0.0;
+  }
   __syncthreads();
   shrink_sorted(a, n, n, 1.1920928955078125e-07, mu, mup, rrank, &s_count, &s_dsum, &s_dlast);
   const int nout = a.ell - 1;
@@ -390,32 +881,33 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
     const int r = rrank[k];
     if (r >= 0 && r < nout) pos[r] = k;
   }
+  if (tid == 0) s_ok = 1;
   __syncthreads();
   const float tnorm = s_tnorm;
-  for (int c0 = 0; c0 < count; c0 += NB) {
-    tri_invit_batch<NB>(A, ld, n, d, e, lam, pos, c0, count, tnorm, scr, piv);
-    __syncthreads();
-  }
-  tri_orthonormalize(A, ld, n, count, hbuf, red);
-  tri_back_transform<VPW>(A, ld, n, count);
-  // rotate-matrix rows: row r = sqrt(mu'/mu) u_r, zero rows past the count
-  float* wr = reinterpret_cast<float*>(a.wrot);
-  for (int idx = tid; idx < nout * n; idx += nt) {
-    const int r = idx / n, i = idx - r * n;
-    float v = 0.f;
-    if (r < count) {
-      const int k = pos[r];
-      const double sc = (mu[k] > 0.0) ? sqrt(mup[k] / mu[k]) : 0.0;
-      v = (float)(sc * (double)*zslot(A, ld, n, r, i));
-    }
-    wr[(size_t)r * a.ldr + i] = v;
-    if (a.wrot_hi) {
-      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-      a.wrot_hi[(size_t)r * a.ldr16 + i] = hi;
-      a.wrot_lo[(size_t)r * a.ldr16 + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
-    }
-  }
+  const float pivmin = fmaxf(tnorm, 1e-30f) * 1e-30f;
+  float* Zt = A + tri_zoff(n);
+  const int ldz = tri_ldz(count);
+  for (int r = tid; r < count; r += nt)
+    if (!tri_twisted(d, e, e2, n, lam[pos[r]], pivmin, Zt + r, ldz)) s_ok = 0;
   __syncthreads();
+  bool ok = s_ok != 0;
+  if (ok) {
+    const int ldc = tri_ldz(count);
+    float* C = reinterpret_cast<float*>(scr_raw);
+    float* dinv = reinterpret_cast<float*>(scr_raw + tri_al16((size_t)(n / 2) * ((n / 2) | 1) * 4));
+    ok = tri_cholqr(Zt, ldz, n, count, C, ldc, dinv, 0.25f);
+  }
+  if (!ok) {
+    __syncthreads();
+    float* scr = reinterpret_cast<float*>(scr_raw);
+    unsigned char* piv = scr_raw + tri_al16((size_t)NB * n * 16);
+    for (int c0 = 0; c0 < count; c0 += NB) {
+      tri_invit_batch<NB>(Zt, ldz, n, d, e, lam, pos, c0, count, tnorm, scr, piv);
+      __syncthreads();
+    }
+    tri_cgs2(Zt, ldz, n, count, xb, red);
+  }
+  tri_back_write<R, MAXJ>(a, A, n, Zt, ldz, count, mu, mup, pos, vb0);  // vb0..pb: 4n floats
   write_counters(a, n, mu, mup, s_count, s_dsum, s_dlast, 0, 1);
 }
 
