@@ -179,7 +179,7 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
     a.ldr = np;
     a.max_sweeps = max_sweeps;
     a.row_mass = s_mass;
-    tri_eig_shrink<TRI_NB, 4, 32>(a, A, ld, nrows, smax > 0.f ? (double)smax : 1.0, smem + REG_A);
+    tri_eig_shrink<TRI_NB, 4, 32, 1>(a, A, ld, nrows, smax > 0.f ? (double)smax : 1.0, smem + REG_A);
   } else {
   float* nrm = reinterpret_cast<float*>(sc);
   double* lam = reinterpret_cast<double*>(sc + BMAX_L * 4);

@@ -314,8 +314,8 @@ __global__ void __launch_bounds__(NT) eig_fast_kernel(EigArgs a) {
 
 // Full-buffer FP32 reductions: Householder tridiagonalisation, bisection and
 // inverse iteration (fd_tridiag.cuh), G scaled by its largest diagonal entry.
-template <int NB, int R, int MAXJ>
-__global__ void __launch_bounds__(512) eig_tri_kernel(EigArgs a) {
+template <int NB, int R, int MAXJ, int VPT>
+__global__ void __launch_bounds__(512, 1) eig_tri_kernel(EigArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = a.n;
   const int ld = n | 1;
@@ -334,20 +334,20 @@ __global__ void __launch_bounds__(512) eig_tri_kernel(EigArgs a) {
   const float inv = (smax > 0.f) ? 1.f / smax : 1.f;
   for (int idx = tid; idx < n * ld; idx += blockDim.x) A[idx] *= inv;
   __syncthreads();
-  tri_eig_shrink<NB, R, MAXJ>(a, A, ld, n, (smax > 0.f) ? (double)smax : 1.0,
+  tri_eig_shrink<NB, R, MAXJ, VPT>(a, A, ld, n, (smax > 0.f) ? (double)smax : 1.0,
                               smem_raw + tri_al16((size_t)n * ld * 4));
 }
 
-template <int NB, int R, int MAXJ>
+template <int NB, int R, int MAXJ, int VPT>
 cudaError_t launch_tri(const EigArgs& a, size_t smem, cudaStream_t st) {
   static size_t attr_set = 0;
   if (smem > attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(eig_tri_kernel<NB, R, MAXJ>,
+    cudaError_t e = cudaFuncSetAttribute(eig_tri_kernel<NB, R, MAXJ, VPT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = smem;
   }
-  eig_tri_kernel<NB, R, MAXJ><<<1, 512, smem, st>>>(a);
+  eig_tri_kernel<NB, R, MAXJ, VPT><<<1, 512, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -393,9 +393,9 @@ cudaError_t launch_eig_shrink(const EigArgs& a, cudaStream_t st) {
   const int np = a.n + (a.n & 1);
   if (sizeof(T) == 4 && a.work == nullptr && a.use_tri) {
     const int cfg = tri_config(a.n, a.ell);
-    if (cfg == 1) return launch_tri<32, 8, 16>(a, tri_smem_bytes(a.n, 32), st);
-    if (cfg == 2) return launch_tri<16, 4, 52>(a, tri_smem_bytes(a.n, 16), st);
-    if (cfg == 3) return launch_tri<8, 4, 52>(a, tri_smem_bytes(a.n, 8), st);
+    if (cfg == 1) return launch_tri<32, 8, 16, 1>(a, tri_smem_bytes(a.n, 32), st);
+    if (cfg == 2) return launch_tri<16, 8, 26, 2>(a, tri_smem_bytes(a.n, 16), st);
+    if (cfg == 3) return launch_tri<8, 8, 26, 2>(a, tri_smem_bytes(a.n, 8), st);
   }
   if (sizeof(T) == 4 && a.work == nullptr && np <= 224 && eig_fast_smem(np) <= 226 * 1024) {
     const size_t smem = eig_fast_smem(np);

@@ -52,17 +52,22 @@ __host__ __device__ constexpr int tri_ldz(int count) { return count | 1; }
 
 // rest-region pieces (bytes)
 __host__ __device__ constexpr size_t tri_scratch_bytes(int n, int NB) {
-  // max of: LU bands + pivots (NB vectors), Cholesky matrix + inverse diagonal
-  // (count <= n/2), Sturm counts of the grid pass (<= 1024 threads)
+  // max of: LU bands + pivots (NB vectors); Cholesky matrix + inverse diagonal
+  // (count <= n/2) and the Sturm counts of the grid pass (<= 1024 threads)
   return (tri_al16((size_t)NB * n * 16) + tri_al16((size_t)NB * n)) >
                  tri_al16((size_t)(n / 2) * ((n / 2) | 1) * 4) + tri_al16((size_t)(n / 2) * 4) + 4096
              ? tri_al16((size_t)NB * n * 16) + tri_al16((size_t)NB * n)
              : tri_al16((size_t)(n / 2) * ((n / 2) | 1) * 4) + tri_al16((size_t)(n / 2) * 4) + 4096;
 }
+// floats of the small-vector region: red (64), five vectors of 8*ceil(n/8)
+// (xb, vb0, vb1, qb, pb), d, e, e2, lam (n each)
+__host__ __device__ constexpr size_t tri_fv_floats(int n) {
+  return 64 + 5 * (size_t)((n + 7) & ~7) + 4 * (size_t)n;
+}
 __host__ __device__ constexpr size_t tri_rest_bytes(int n, int NB) {
   return tri_scratch_bytes(n, NB) + tri_al16((size_t)n * 16)  // mu, mup
-         + tri_al16((size_t)(9 * n + 64) * 4)                 // d e e2 lam xb vb0 vb1 qb pb, red
-         + tri_al16((size_t)(2 * n + 16) * 4);                // rrank pos
+         + tri_al16(tri_fv_floats(n) * 4)                      // small vectors
+         + tri_al16((size_t)(2 * n + 16) * 4);                 // rrank pos
 }
 // Shared-memory bytes of the whole solve for n rows (A with stride n | 1).
 __host__ __device__ constexpr size_t tri_smem_bytes(int n, int NB) {
@@ -73,6 +78,24 @@ __host__ __device__ constexpr size_t tri_smem_bytes(int n, int NB) {
 // Step 1. d (n) and e (n-1) receive T; xb, vb0, vb1, qb, pb: n floats each;
 // red: 64 floats.
 // ---------------------------------------------------------------------------
+// Sum of the first nw (<= 32, a multiple of 4 or less than 4... any) floats
+// of a 16-byte aligned shared array: four-wide loads and a tree, so the
+// result waits on one load latency instead of nw dependent ones.
+__device__ __forceinline__ float tri_sum_parts(const float* p, int nw) {
+  float s[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (4 * q < nw) {
+      const float4 v = reinterpret_cast<const float4*>(p)[q];
+      s[q] = (4 * q + 3 < nw) ? (v.x + v.y) + (v.z + v.w)
+                              : v.x + (4 * q + 1 < nw ? v.y : 0.f) + (4 * q + 2 < nw ? v.z : 0.f);
+    } else {
+      s[q] = 0.f;
+    }
+  }
+  return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+}
+
 static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, float* xb,
                                   float* vb0, float* vb1, float* qb, float* pb, float* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -96,8 +119,7 @@ static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, f
     float* vcur = (s & 1) ? vb1 : vb0;
     const float* vprv = (s & 1) ? vb0 : vb1;
     // reflector s: v = (x - alpha e_1) / ||x - alpha e_1||, alpha = -sign(x_0) ||x||
-    float ss = 0.f;
-    for (int w = 0; w < nw; ++w) ss += npart[w];
+    const float ss = tri_sum_parts(npart, nw);
     const float x0 = xb[0];
     float alpha = x0, scale = 0.f;  // a length-1 (or zero) column needs no reflection
     if (m > 1 && ss > 0.f) {
@@ -193,8 +215,7 @@ static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, f
     // q_s, and column s+1 updated by step s: its diagonal is d[s+1], the
     // rest is x_{s+1}
     {
-      float K = 0.f;
-      for (int w = 0; w < nw; ++w) K += kpart[w];
+      const float K = tri_sum_parts(kpart, nw);
       const float v0 = vcur[0];
       const float q0 = 2.f * fmaf(-K, v0, pb[0]);
       float sq = 0.f;
@@ -462,8 +483,9 @@ static __device__ bool tri_twisted(const float* d, const float* e, const float* 
 // Zt <- Zt L^-T. Returns false, with Zt unchanged, if a pivot of C is below
 // tau (uniform across the block).
 // ---------------------------------------------------------------------------
-static __device__ bool tri_cholqr(float* Zt, int ldz, int n, int count, float* C, int ldc,
-                                  float* dinv, float tau) {
+template <int U>  // panel rows per lane: count <= 32 U
+__device__ bool tri_cholqr(float* Zt, int ldz, int n, int count, float* C, int ldc, float* dinv,
+                           float tau) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nb = (count + 3) >> 2;
   const int ntile = nb * (nb + 1) / 2;
@@ -499,25 +521,93 @@ static __device__ bool tri_cholqr(float* Zt, int ldz, int n, int count, float* C
         if (a0 + p < count && b0 + q <= a0 + p) C[(size_t)(a0 + p) * ldc + b0 + q] = acc[p][q];
   }
   __syncthreads();
-  // right-looking Cholesky; the trailing update of column j runs over all
-  // (i, k), j < k <= i < count, flattened across the block
-  for (int j = 0; j < count; ++j) {
-    const float piv = C[(size_t)j * ldc + j];  // not written during step j
-    if (!(piv >= tau)) return false;           // same value in every thread
-    const float rinv = 1.f / sqrtf(piv);
-    for (int i = j + 1 + tid; i < count; i += nt) C[(size_t)i * ldc + j] *= rinv;
-    if (tid == 0) dinv[j] = rinv;
+  // Right-looking Cholesky by panels of 8 columns. Warp 0 factors a panel in
+  // registers (lane l holds rows j0 + l + 32 u), then all threads update the
+  // trailing lower triangle with 4x4 tiles.
+  __shared__ int s_ok;
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int j0 = 0; j0 < count; j0 += 8) {
+    const int jb = min(8, count - j0);
+    if (warp == 0) {
+      float P[U][8];
+      int ok = 1;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = j0 + lane + 32 * u;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+          P[u][jj] = (i < count && jj < jb && i >= j0 + jj) ? C[(size_t)i * ldc + j0 + jj] : 0.f;
+      }
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        if (jj < jb) {
+          const float piv = __shfl_sync(0xffffffffu, P[0][jj], jj);
+          if (!(piv >= tau)) ok = 0;
+          const float rinv = ok ? 1.f / sqrtf(piv) : 0.f;
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (lane + 32 * u > jj) P[u][jj] *= rinv;
+          if (lane == 0) dinv[j0 + jj] = rinv;
+#pragma unroll
+          for (int kk = jj + 1; kk < 8; ++kk) {
+            const float lk = __shfl_sync(0xffffffffu, P[0][jj], kk);  // l_{j0+kk, jj}
+            if (kk < jb)
+#pragma unroll
+              for (int u = 0; u < U; ++u)
+                if (lane + 32 * u >= kk) P[u][kk] = fmaf(-P[u][jj], lk, P[u][kk]);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = j0 + lane + 32 * u;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+          if (i < count && jj < jb && i > j0 + jj) C[(size_t)i * ldc + j0 + jj] = P[u][jj];
+      }
+      if (lane == 0) s_ok = ok;
+    }
     __syncthreads();
-    const int mm = count - 1 - j;
-    const int tot = mm * (mm + 1) / 2;
-    for (int t = tid; t < tot; t += nt) {
-      int ii = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
-      while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-      while (ii * (ii + 1) / 2 > t) --ii;
-      const int kk = t - ii * (ii + 1) / 2;
-      const int i = j + 1 + ii, k = j + 1 + kk;
-      C[(size_t)i * ldc + k] =
-          fmaf(-C[(size_t)i * ldc + j], C[(size_t)k * ldc + j], C[(size_t)i * ldc + k]);
+    if (!s_ok) return false;  // same value in every thread
+    // trailing update: C[i][k] -= sum_jj L[i][j0+jj] L[k][j0+jj], j0+jb <= k <= i < count
+    const int t0 = j0 + jb;
+    const int nb4 = (count - t0 + 3) >> 2;
+    const int ntl = nb4 * (nb4 + 1) / 2;
+    for (int t = tid; t < ntl; t += nt) {
+      int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+      while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+      while (ti * (ti + 1) / 2 > t) --ti;
+      const int tk = t - ti * (ti + 1) / 2;
+      const int i0 = t0 + 4 * ti, k0 = t0 + 4 * tk;
+      float acc16[4][4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc16[p][q] = 0.f;
+#pragma unroll
+      for (int h = 0; h < 8; h += 4) {
+        float li[4][4], lk[4][4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            li[p][jj] = (i0 + p < count && h + jj < jb) ? C[(size_t)(i0 + p) * ldc + j0 + h + jj] : 0.f;
+            lk[p][jj] = (k0 + p < count && h + jj < jb) ? C[(size_t)(k0 + p) * ldc + j0 + h + jj] : 0.f;
+          }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) acc16[p][q] = fmaf(li[p][jj], lk[q][jj], acc16[p][q]);
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = i0 + p, k = k0 + q;
+          if (i < count && k <= i) C[(size_t)i * ldc + k] -= acc16[p][q];
+        }
     }
     __syncthreads();
   }
@@ -657,6 +747,151 @@ __device__ void tri_invit_batch(float* Zt, int ldz, int n, const float* d, const
 #undef Z
 }
 
+// Fallback of steps 3-4 for clusters (LAPACK-style inverse iteration): the
+// retained positions are ordered by eigenvalue and split into clusters where
+// neighbours are closer than gtol. The members of each cluster of two or more
+// are recomputed one after another by one thread: LU with partial pivoting of
+// T - (lambda + k * shift) I (k = index in the cluster), then five steps of
+// "solve, orthogonalise against the members already done (modified
+// Gram-Schmidt), normalise". Clusters run in parallel, NB at a time. Single
+// vectors keep their twisted solution. ord: count ints; cbeg: 2 ints per
+// cluster (at most count).
+template <int NB>
+__device__ void tri_invit_clusters(float* Zt, int ldz, int n, const float* d, const float* e,
+                                   const float* lam, const int* pos, int count, float tnorm,
+                                   float gtol, float* scr, unsigned char* piv, int* ord,
+                                   int* cbeg) {
+  const int tid = threadIdx.x;
+  __shared__ int s_ncl;
+  if (tid == 0) {
+    // order by position (positions are sorted by eigenvalue, descending)
+    int k = 0;
+    for (int q = 0; q < n && k < count; ++q)
+      for (int r = 0; r < count; ++r)
+        if (pos[r] == q) ord[k++] = r;
+    int ncl = 0;
+    for (int a = 0; a < count;) {
+      int b = a + 1;
+      while (b < count && lam[pos[ord[b - 1]]] - lam[pos[ord[b]]] <= gtol) ++b;
+      if (b - a >= 2) cbeg[2 * ncl] = a, cbeg[2 * ncl + 1] = b, ++ncl;
+      a = b;
+    }
+    s_ncl = ncl;
+  }
+  __syncthreads();
+  const int ncl = s_ncl;
+  const float eps = 1.1920929e-07f;
+  const float tiny = eps * fmaxf(tnorm, 1e-30f);
+  const float shift = 16.f * eps * fmaxf(tnorm, 1e-30f);
+  for (int c0 = 0; c0 < ncl; c0 += NB) {
+    const int t = tid, ci = c0 + t;
+    if (t < NB && ci < ncl) {
+      float* dd = scr;
+      float* du = scr + (size_t)NB * n;
+      float* du2 = scr + (size_t)2 * NB * n;
+      float* dl = scr + (size_t)3 * NB * n;
+#define DD(i) dd[(size_t)(i) * NB + t]
+#define DU(i) du[(size_t)(i) * NB + t]
+#define DU2(i) du2[(size_t)(i) * NB + t]
+#define DL(i) dl[(size_t)(i) * NB + t]
+#define PV(i) piv[(size_t)(i) * NB + t]
+      const int a = cbeg[2 * ci], b = cbeg[2 * ci + 1];
+      for (int mi = a; mi < b; ++mi) {
+        const int c = ord[mi];
+        float* z = Zt + c;
+        const float lmb = lam[pos[c]] + (float)(mi - a) * shift;
+        for (int i = 0; i < n; ++i) {
+          DD(i) = d[i] - lmb;
+          if (i < n - 1) {
+            DU(i) = e[i];
+            DL(i) = e[i];
+            DU2(i) = 0.f;
+          }
+        }
+        for (int i = 0; i + 1 < n; ++i) {
+          const float di = DD(i), li = DL(i);
+          if (fabsf(di) >= fabsf(li)) {
+            const float dv = (di == 0.f) ? tiny : di;
+            DD(i) = dv;
+            const float f = li / dv;
+            DL(i) = f;
+            DD(i + 1) = DD(i + 1) - f * DU(i);
+            PV(i) = 0;
+          } else {
+            const float f = di / li;
+            DD(i) = li;
+            DL(i) = f;
+            const float tmp = DU(i);
+            const float dn = DD(i + 1);
+            DU(i) = dn;
+            DD(i + 1) = tmp - f * dn;
+            if (i + 2 < n) {
+              DU2(i) = DU(i + 1);
+              DU(i + 1) = -f * DU(i + 1);
+            }
+            PV(i) = 1;
+          }
+        }
+        if (DD(n - 1) == 0.f) DD(n - 1) = tiny;
+        for (int i = 0; i < n; ++i) {  // start: ones with a deterministic perturbation
+          unsigned h = (unsigned)(i * 2654435761u) ^ (unsigned)(c * 40503u + 0x9e3779b9u);
+          h ^= h >> 15;
+          h *= 2246822519u;
+          h ^= h >> 13;
+          z[(size_t)i * ldz] = 1.f + 0.25f * ((float)(h & 0xffff) / 65536.f - 0.5f);
+        }
+        for (int rep = 0; rep < 5; ++rep) {
+          for (int i = 0; i + 1 < n; ++i) {
+            const float zi = z[(size_t)i * ldz], zj = z[(size_t)(i + 1) * ldz];
+            if (!PV(i)) {
+              z[(size_t)(i + 1) * ldz] = zj - DL(i) * zi;
+            } else {
+              z[(size_t)i * ldz] = zj;
+              z[(size_t)(i + 1) * ldz] = zi - DL(i) * zj;
+            }
+          }
+          float x2 = 0.f, x1 = 0.f;
+          for (int i = n - 1; i >= 0; --i) {
+            float v = z[(size_t)i * ldz];
+            if (i + 1 < n) v -= DU(i) * x1;
+            if (i + 2 < n) v -= DU2(i) * x2;
+            v /= DD(i);
+            z[(size_t)i * ldz] = v;
+            x2 = x1;
+            x1 = v;
+          }
+          float mx = 0.f;
+          for (int i = 0; i < n; ++i) mx = fmaxf(mx, fabsf(z[(size_t)i * ldz]));
+          const float inv = (mx > 0.f) ? 1.f / mx : 1.f;
+          for (int i = 0; i < n; ++i) z[(size_t)i * ldz] *= inv;
+          for (int pj = a; pj < mi; ++pj) {  // against the members already done
+            const float* y = Zt + ord[pj];
+            float h0 = 0.f, h1 = 0.f;
+            int i = 0;
+            for (; i + 1 < n; i += 2) {
+              h0 = fmaf(z[(size_t)i * ldz], y[(size_t)i * ldz], h0);
+              h1 = fmaf(z[(size_t)(i + 1) * ldz], y[(size_t)(i + 1) * ldz], h1);
+            }
+            if (i < n) h0 = fmaf(z[(size_t)i * ldz], y[(size_t)i * ldz], h0);
+            const float hh = h0 + h1;
+            for (int k = 0; k < n; ++k) z[(size_t)k * ldz] = fmaf(-hh, y[(size_t)k * ldz], z[(size_t)k * ldz]);
+          }
+          float s2 = 0.f;
+          for (int i = 0; i < n; ++i) s2 = fmaf(z[(size_t)i * ldz], z[(size_t)i * ldz], s2);
+          const float r = 1.f / sqrtf(fmaxf(s2, 1e-30f));
+          for (int i = 0; i < n; ++i) z[(size_t)i * ldz] *= r;
+        }
+      }
+#undef DD
+#undef DU
+#undef DU2
+#undef DL
+#undef PV
+    }
+    __syncthreads();
+  }
+}
+
 __device__ __forceinline__ float tri_block_sum(float v, float* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = (blockDim.x + 31) >> 5;
@@ -710,9 +945,10 @@ static __device__ void tri_cgs2(float* Zt, int ldz, int n, int count, float* hbu
 // block H_{s-3} H_{s-2} H_{s-1} H_s z with a_k = v_{s-k},
 //   h_k = a_k . z,  g_k = h_k - 2 sum_{j<k} g_j (a_k . a_j),  z -= 2 sum_k g_k a_k,
 // the six products a_k . a_j of every block being formed first (mw: 6 per
-// block). Rows count..ell-2 of the output are zero.
+// block). VPT: vectors per thread (1 or 2; with 2, each reflector load
+// feeds both). Rows count..ell-2 of the output are zero.
 // ---------------------------------------------------------------------------
-template <int R, int MAXJ>
+template <int R, int MAXJ, int VPT>
 __device__ void tri_back_write(const EigArgs& a, const float* V, int n, const float* Zt, int ldz,
                                int count, const double* mu, const double* mup, const int* pos,
                                float* mw) {
@@ -736,6 +972,7 @@ __device__ void tri_back_write(const EigArgs& a, const float* V, int n, const fl
     if (lane == 0) mw[w] = sum;
   }
   __syncthreads();
+  if constexpr (VPT == 1) {
   const int per = nt / R;
   for (int cb = 0; cb < count; cb += per) {  // uniform across the block
     const int c = cb + tid / R, g = tid % R;
@@ -821,6 +1058,150 @@ __device__ void tri_back_write(const EigArgs& a, const float* V, int n, const fl
       }
     }
   }
+  } else {
+  // thread (pair p, g): vectors 2p and 2p+1, rows i = n-1-(g + R j)
+  const int per = nt / R;  // vector pairs per pass
+  for (int cb = 0; cb < count; cb += 2 * per) {  // uniform across the block
+    const int c0 = cb + 2 * (tid / R), g = tid % R;
+    const bool act0 = c0 < count, act1 = c0 + 1 < count;
+    float z0[MAXJ], z1[MAXJ];
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j) {
+      const int i = n - 1 - (g + R * j);
+      z0[j] = (act0 && i >= 0) ? Zt[(size_t)i * ldz + c0] : 0.f;
+      z1[j] = (act1 && i >= 0) ? Zt[(size_t)i * ldz + c0 + 1] : 0.f;
+    }
+    for (int b = 0; b < nblk; ++b) {
+      const int sb = n - 3 - 4 * b;
+      int je[4];
+      const float* ap[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int sk = sb - k;
+        je[k] = (sk >= 0) ? (n - 1 - sk - g + R - 1) / R : 0;  // rows i > sk: j < je[k]
+        const int sc = sk >= 0 ? sk : 0;
+        ap[k] = V + tri_voff(n, sc) - (sc + 1) + (n - 1 - g);  // a_k[i_j] = ap[k][-R j]
+      }
+      // rows j < jall are touched by all four reflectors (none in a partial block)
+      const int jall = (sb - 3 >= 0) ? je[0] : 0;
+      const int jmx = max(max(je[0], je[1]), max(je[2], je[3]));
+      float h0[4] = {0.f, 0.f, 0.f, 0.f}, h1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int jc = 0; jc < MAXJ; jc += 4) {
+        if (jc >= jmx) break;
+        if (jc + 4 <= jall) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = jc + u;
+            if (j < MAXJ) {
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const float av = ap[k][-R * j];
+                h0[k] = fmaf(av, z0[j], h0[k]);
+                h1[k] = fmaf(av, z1[j], h1[k]);
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = jc + u;
+            if (j < MAXJ) {
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const float av = (j < je[k]) ? ap[k][-R * j] : 0.f;
+                h0[k] = fmaf(av, z0[j], h0[k]);
+                h1[k] = fmaf(av, z1[j], h1[k]);
+              }
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 1; o < R; o <<= 1)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          h0[k] += __shfl_xor_sync(0xffffffffu, h0[k], o);
+          h1[k] += __shfl_xor_sync(0xffffffffu, h1[k], o);
+        }
+      const float* m6 = mw + 6 * b;
+      float t0[4], t1[4];
+      {
+        const float g0 = h0[0];
+        const float g1 = h0[1] - 2.f * g0 * m6[0];
+        const float g2 = h0[2] - 2.f * (g0 * m6[1] + g1 * m6[2]);
+        const float g3 = h0[3] - 2.f * (g0 * m6[3] + g1 * m6[4] + g2 * m6[5]);
+        t0[0] = 2.f * g0; t0[1] = 2.f * g1; t0[2] = 2.f * g2; t0[3] = 2.f * g3;
+      }
+      {
+        const float g0 = h1[0];
+        const float g1 = h1[1] - 2.f * g0 * m6[0];
+        const float g2 = h1[2] - 2.f * (g0 * m6[1] + g1 * m6[2]);
+        const float g3 = h1[3] - 2.f * (g0 * m6[3] + g1 * m6[4] + g2 * m6[5]);
+        t1[0] = 2.f * g0; t1[1] = 2.f * g1; t1[2] = 2.f * g2; t1[3] = 2.f * g3;
+      }
+#pragma unroll
+      for (int jc = 0; jc < MAXJ; jc += 4) {
+        if (jc >= jmx) break;
+        if (jc + 4 <= jall) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = jc + u;
+            if (j < MAXJ) {
+              float u0 = 0.f, u1 = 0.f;
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const float av = ap[k][-R * j];
+                u0 = fmaf(t0[k], av, u0);
+                u1 = fmaf(t1[k], av, u1);
+              }
+              z0[j] -= u0;
+              z1[j] -= u1;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = jc + u;
+            if (j < MAXJ) {
+              float u0 = 0.f, u1 = 0.f;
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const float av = (j < je[k]) ? ap[k][-R * j] : 0.f;
+                u0 = fmaf(t0[k], av, u0);
+                u1 = fmaf(t1[k], av, u1);
+              }
+              z0[j] -= u0;
+              z1[j] -= u1;
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = c0 + h;
+      if (c < count) {
+        const int k = pos[c];
+        const double sc = (mu[k] > 0.0) ? sqrt(mup[k] / mu[k]) : 0.0;
+        if (a.row_mass && g == 0) a.row_mass[c] = mup[k];
+#pragma unroll
+        for (int j = 0; j < MAXJ; ++j) {
+          const int i = n - 1 - (g + R * j);
+          if (i >= 0) {
+            const float val = (float)(sc * (double)(h ? z1[j] : z0[j]));
+            wr[(size_t)c * a.ldr + i] = val;
+            if (a.wrot_hi) {
+              const __nv_bfloat16 hi = __float2bfloat16_rn(val);
+              a.wrot_hi[(size_t)c * a.ldr16 + i] = hi;
+              a.wrot_lo[(size_t)c * a.ldr16 + i] = __float2bfloat16_rn(val - __bfloat162float(hi));
+            }
+          }
+        }
+      }
+    }
+  }
+  }
   if (a.row_mass)
     for (int r = count + tid; r < nout; r += nt) a.row_mass[r] = 0.0;
   for (int idx = tid; idx < (nout - count) * n; idx += nt) {
@@ -840,26 +1221,28 @@ __device__ void tri_back_write(const EigArgs& a, const float* V, int n, const fl
 // NB: vectors per fallback inverse-iteration batch; R, MAXJ: step-5 layout
 // (n <= R * MAXJ, R * min(count, nt / R) <= nt).
 // ---------------------------------------------------------------------------
-template <int NB, int R, int MAXJ>
+template <int NB, int R, int MAXJ, int VPT>
 __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double smax,
                                unsigned char* rest) {
+  constexpr int TRI_CU = (R * MAXJ / 2 + 31) / 32;  // retained vectors <= n / 2 <= 32 TRI_CU
   const int tid = threadIdx.x, nt = blockDim.x;
   unsigned char* scr_raw = rest;
   double* mu = reinterpret_cast<double*>(rest + tri_scratch_bytes(n, NB));
   double* mup = mu + n;
   float* fv = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(mu) + tri_al16((size_t)n * 16));
-  float* d = fv;
+  const int np8 = (n + 7) & ~7;
+  float* red = fv;  // 64 floats, 16-byte aligned (read four at a time)
+  float* xb = red + 64;
+  float* vb0 = xb + np8;
+  float* vb1 = vb0 + np8;
+  float* qb = vb1 + np8;
+  float* pb = qb + np8;
+  float* d = pb + np8;
   float* e = d + n;
   float* e2 = e + n;
   float* lam = e2 + n;
-  float* xb = lam + n;
-  float* vb0 = xb + n;
-  float* vb1 = vb0 + n;
-  float* qb = vb1 + n;
-  float* pb = qb + n;
-  float* red = pb + n;  // 64 floats
   int* rrank = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(fv) +
-                                      tri_al16((size_t)(9 * n + 64) * 4));
+                                      tri_al16(tri_fv_floats(n) * 4));
   int* pos = rrank + n;
   __shared__ float s_tnorm;
   __shared__ int s_count, s_ok;
@@ -895,19 +1278,33 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
     const int ldc = tri_ldz(count);
     float* C = reinterpret_cast<float*>(scr_raw);
     float* dinv = reinterpret_cast<float*>(scr_raw + tri_al16((size_t)(n / 2) * ((n / 2) | 1) * 4));
-    ok = tri_cholqr(Zt, ldz, n, count, C, ldc, dinv, 0.25f);
+    ok = tri_cholqr<TRI_CU>(Zt, ldz, n, count, C, ldc, dinv, 0.25f);
   }
   if (!ok) {
+    // clusters recomputed with reorthogonalisation, then Cholesky-QR again;
+    // classical Gram-Schmidt (twice) if that still fails
     __syncthreads();
     float* scr = reinterpret_cast<float*>(scr_raw);
     unsigned char* piv = scr_raw + tri_al16((size_t)NB * n * 16);
-    for (int c0 = 0; c0 < count; c0 += NB) {
-      tri_invit_batch<NB>(Zt, ldz, n, d, e, lam, pos, c0, count, tnorm, scr, piv);
-      __syncthreads();
+    if (s_ok) {
+      tri_invit_clusters<NB>(Zt, ldz, n, d, e, lam, pos, count, tnorm, 1e-4f * tnorm, scr, piv,
+                             reinterpret_cast<int*>(pb), reinterpret_cast<int*>(pb) + (count + 1));
+    } else {
+      for (int c0 = 0; c0 < count; c0 += NB) {
+        tri_invit_batch<NB>(Zt, ldz, n, d, e, lam, pos, c0, count, tnorm, scr, piv);
+        __syncthreads();
+      }
     }
-    tri_cgs2(Zt, ldz, n, count, xb, red);
+    const int ldc = tri_ldz(count);
+    float* C = reinterpret_cast<float*>(scr_raw);
+    float* dinv = reinterpret_cast<float*>(scr_raw + tri_al16((size_t)(n / 2) * ((n / 2) | 1) * 4));
+    __syncthreads();
+    if (!tri_cholqr<TRI_CU>(Zt, ldz, n, count, C, ldc, dinv, 0.25f)) {
+      __syncthreads();
+      tri_cgs2(Zt, ldz, n, count, xb, red);
+    }
   }
-  tri_back_write<R, MAXJ>(a, A, n, Zt, ldz, count, mu, mup, pos, vb0);  // vb0..pb: 4n floats
+  tri_back_write<R, MAXJ, VPT>(a, A, n, Zt, ldz, count, mu, mup, pos, vb0);  // vb0..pb: 4 np8 floats
   write_counters(a, n, mu, mup, s_count, s_dsum, s_dlast, 0, 1);
 }
 

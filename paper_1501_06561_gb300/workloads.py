@@ -165,8 +165,11 @@ def random_noisy_device(n: int, d: int, m: int, seed: int, zeta: float = 10.0,
     dtype = torch.bfloat16 if dtype is None else dtype
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
-    q, r = torch.linalg.qr(torch.randn(d, m, generator=g, device=device, dtype=torch.float32))
-    q = q * torch.sign(torch.diagonal(r))[None, :]
+    # the d x m orthonormal factor is small: QR on the host (no device
+    # linear-algebra library needed), Gaussian drawn from the device stream
+    gauss = torch.randn(d, m, generator=g, device=device, dtype=torch.float32).cpu().double()
+    q, r = torch.linalg.qr(gauss)
+    q = (q * torch.sign(torch.diagonal(r))[None, :]).float().to(device)
     Dg = torch.linspace(1.0, 0.1, m, device=device) if m > 1 else torch.ones(1, device=device)
     DU = Dg[:, None] * q.T
     if out is None:
