@@ -32,6 +32,8 @@ const char* cuda_error_text() {
 
 int gram_simt_slices(int64_t d, int ksplit);
 bool eig_fits_smem(int n, size_t elem);
+int tri_config(int n, int ell);
+size_t tri_global_workspace(int n);
 
 // tensor-core path (fd_tc.cu)
 struct TcCtx;
@@ -77,6 +79,7 @@ struct fd_state {
   int ldp = 0;
   int ksplit = 1;
   void* work = nullptr;   // eigensolve matrix in global memory when it does not fit smem
+  size_t work_bytes = 0;
   void* wrot = nullptr;   // rotate matrix (ell-1) x ldr
   int ldr = 0;
   void* sk = nullptr;     // flush output, ell x ldb
@@ -224,11 +227,16 @@ extern "C" int fd_create(int64_t d, int32_t ell, int32_t variant, double alpha, 
     h->ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(kt, 304 / (tiles * tiles)));
     const int slices = gram_simt_slices(d, h->ksplit);
     FD_ALLOC(h->parts, (size_t)slices * h->ldp * h->ldp * h->es);
-    if (!eig_fits_smem(h->L, h->es)) FD_ALLOC(h->work, (size_t)(np + 1) * (np + 1) * h->es);
+    size_t wb = eig_fits_smem(h->L, h->es) ? 0 : (size_t)(np + 1) * (np + 1) * h->es;
+    if (prec == FD_PREC_FP32 && tri_config(h->L, ell) == 4)
+      wb = std::max(wb, tri_global_workspace(h->L));
+    if (wb) { FD_ALLOC(h->work, wb); h->work_bytes = wb; }
   } else {
     int rc = tc_create(&h->tc, d, ell, h->st);
     if (rc != FD_OK) { free_state(h); return rc; }
-    if (!eig_fits_smem(h->L, 4)) FD_ALLOC(h->work, (size_t)(np + 1) * (np + 1) * 4);
+    size_t wb = eig_fits_smem(h->L, 4) ? 0 : (size_t)(np + 1) * (np + 1) * 4;
+    if (tri_config(h->L, ell) == 4) wb = std::max(wb, tri_global_workspace(h->L));
+    if (wb) { FD_ALLOC(h->work, wb); h->work_bytes = wb; }
   }
   h->ldr = (h->L + 63) / 64 * 64;
   FD_ALLOC(h->wrot, (size_t)ell * h->ldr * h->es);
@@ -268,6 +276,7 @@ static int reduce_rows(fd_state* h, int nrows, void* out, int64_t ldo, DevCounte
   a.variant = h->variant;
   a.alpha = h->alpha;
   a.work = h->work;
+  a.work_bytes = h->work_bytes;
   a.ldw_work = nrows + (nrows & 1);
   a.ctr_in = h->ctr;
   a.ctr_out = ctr_out;

@@ -74,7 +74,6 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
   float* A = reinterpret_cast<float*>(smem);
   float* Bst = reinterpret_cast<float*>(smem + REG_A);
   __shared__ double s_mass[BMAX_L / 2];       // sigma'^2 of each output row
-  __shared__ float s_rsum[BT / 32][BMAX_L / 2 * RCH / BT];  // per-warp row sums of squares
   unsigned char* sc = smem + REG_A + REG_B;
   const int np = nrows + (nrows & 1);
   const int npb = (np + 7) & ~7;  // block Jacobi pads to whole 4-column block pairs
@@ -179,7 +178,8 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
     a.ldr = np;
     a.max_sweeps = max_sweeps;
     a.row_mass = s_mass;
-    tri_eig_shrink<TRI_NB, 4, 32, 1>(a, A, ld, nrows, smax > 0.f ? (double)smax : 1.0, smem + REG_A);
+    tri_eig_shrink<TRI_NB, 4, 32, 1, 4>(a, A, ld, nrows, smax > 0.f ? (double)smax : 1.0, smem + REG_A,
+                                        smem + REG_A + tri_scratch_bytes(nrows, TRI_NB));
   } else {
   float* nrm = reinterpret_cast<float*>(sc);
   double* lam = reinterpret_cast<double*>(sc + BMAX_L * 4);
@@ -214,15 +214,13 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
   __syncthreads();
 
   // ---- rotate: out[r][c] = sum_i W[r][i] B[i][c], column chunks staged in A ----
-  // Thread tid computes rows r = tid / RCH + (BT / RCH) k of column c = tid % RCH
-  // in every chunk and keeps their sums of squares.
-  constexpr int RK = BMAX_L / 2 * RCH / BT;  // row slots per thread
-  static_assert(BT % RCH == 0 && RCH % 32 == 0, "rotate layout");
+  // The squares of every output are summed per (row, chunk column) in shared
+  // memory behind the staging area (each slot has one owner: a fixed order).
   const int nout = S.ell - 1;
   float* W = Bst;
-  float rss[RK];
-#pragma unroll
-  for (int k = 0; k < RK; ++k) rss[k] = 0.f;
+  float* sq = A + BMAX_L * RCH;  // nout x RCH sums of squares
+  static_assert((size_t)(BMAX_L + BMAX_L / 2) * RCH * 4 <= REG_A, "rotate staging");
+  for (int idx = tid; idx < nout * RCH; idx += BT) sq[idx] = 0.f;
   for (long long c0 = 0; c0 < d; c0 += RCH) {
     __syncthreads();
     for (int idx = tid; idx < nrows * RCH; idx += BT) {
@@ -230,53 +228,43 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
       A[r * RCH + c] = (c0 + c < d) ? buf[(long long)r * ldb + c0 + c] : 0.f;
     }
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < RK; ++k) {
-      const int idx = tid + k * BT;
-      if (idx < nout * RCH) {
-        const int r = idx / RCH, c = idx % RCH;
-        float s0 = 0.f, s1 = 0.f;
-        const float* wr = W + r * np;
-        int i = 0;
-        for (; i + 1 < nrows; i += 2) {
-          s0 = fmaf(wr[i], A[i * RCH + c], s0);
-          s1 = fmaf(wr[i + 1], A[(i + 1) * RCH + c], s1);
-        }
-        if (i < nrows) s0 = fmaf(wr[i], A[i * RCH + c], s0);
-        if (c0 + c < d) {
-          const float v = s0 + s1;
-          out[(long long)r * ldo + c0 + c] = v;
-          rss[k] = fmaf(v, v, rss[k]);
-        }
+    for (int idx = tid; idx < nout * RCH; idx += BT) {
+      const int r = idx / RCH, c = idx % RCH;
+      float s0 = 0.f, s1 = 0.f;
+      const float* wr = W + r * np;
+      int i = 0;
+      for (; i + 1 < nrows; i += 2) {
+        s0 = fmaf(wr[i], A[i * RCH + c], s0);
+        s1 = fmaf(wr[i + 1], A[(i + 1) * RCH + c], s1);
+      }
+      if (i < nrows) s0 = fmaf(wr[i], A[i * RCH + c], s0);
+      if (c0 + c < d) {
+        const float v = s0 + s1;
+        out[(long long)r * ldo + c0 + c] = v;
+        sq[idx] = fmaf(v, v, sq[idx]);
       }
     }
   }
+  __syncthreads();
   // A row of S'V^T has norm sigma' exactly (Alg. 1): rescale each output row
   // to its FP64 target sigma'^2. This removes the error that the ratio
   // sigma'^2 / sigma^2 would otherwise amplify (large for SS merges into a
-  // small direction). Row sums are combined in a fixed order.
+  // small direction).
+  __shared__ float s_rscale[BMAX_L / 2];
   {
     const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-    for (int k = 0; k < RK; ++k) {
-      const float v = warp_sum(rss[k]);
-      if (lane == 0) s_rsum[warp][k] = v;
+    for (int r = warp; r < nout; r += BT / 32) {
+      float t = 0.f;
+      for (int c = lane; c < RCH; c += 32) t += sq[r * RCH + c];
+      t = warp_sum(t);
+      if (lane == 0) s_rscale[r] = (t > 0.f) ? (float)sqrt(s_mass[r] / (double)t) : 1.f;
     }
-  }
-  __syncthreads();
-  float* rscale = reinterpret_cast<float*>(A);  // staging area is dead now
-  for (int r = tid; r < nout; r += BT) {
-    const int q = r % (BT / RCH), k = r / (BT / RCH);
-    constexpr int WPR = RCH / 32;  // warps per row group
-    float tot = 0.f;
-    for (int w = 0; w < WPR; ++w) tot += s_rsum[q * WPR + w][k];
-    rscale[r] = (tot > 0.f) ? (float)sqrt(s_mass[r] / (double)tot) : 1.f;
   }
   __syncthreads();
   for (long long idx = tid; idx < (long long)nout * d; idx += BT) {
     const int r = (int)(idx / d);
     const long long c = idx - (long long)r * d;
-    out[(long long)r * ldo + c] *= rscale[r];
+    out[(long long)r * ldo + c] *= s_rscale[r];
   }
   __syncthreads();
 }
@@ -723,6 +711,7 @@ struct fd_server_state {
   std::vector<char> busy_stream;
   int next_stream = 0;
   std::vector<char> inflight;       // per sketch
+  int in_transit = 0;               // requests taken from pending, not yet in launches
   std::deque<ServeReq> pending;
   std::deque<ServeLaunch> launches;
   std::vector<std::pair<int64_t, double>> done;  // (ticket, latency s)
@@ -811,6 +800,7 @@ static void serve_engine(fd_server_state* s) {
         if (!take.empty()) {
           s->busy_stream[st] = 1;
           s->next_stream = (st + 1) % s->nstreams;
+          s->in_transit += (int)take.size();
         }
       }
       if (take.empty()) {
@@ -848,6 +838,7 @@ static void serve_engine(fd_server_state* s) {
         s->b->nseen[r.id] += r.n;
       }
       s->launched += 1;
+      s->in_transit -= (int)L.reqs.size();
       s->launches.push_back(std::move(L));
     }
     if (cudaGetLastError() != cudaSuccess) s->err = 1;
@@ -938,7 +929,7 @@ extern "C" int fd_serve_drain(fd_server_state* s) {
   for (;;) {
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      if (s->pending.empty() && s->launches.empty()) break;
+      if (s->pending.empty() && s->launches.empty() && s->in_transit == 0) break;
     }
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }

@@ -37,6 +37,7 @@ struct EigArgs {
   double alpha;
   void* work;          // global G when it does not fit in shared memory (n x ldw)
   int ldw_work;
+  size_t work_bytes;   // size of work
   const DevCounters* ctr_in;
   DevCounters* ctr_out;
   double* sig2_out;    // sorted sigma^2 (n) or null

@@ -314,13 +314,18 @@ __global__ void __launch_bounds__(NT) eig_fast_kernel(EigArgs a) {
 
 // Full-buffer FP32 reductions: Householder tridiagonalisation, bisection and
 // inverse iteration (fd_tridiag.cuh), G scaled by its largest diagonal entry.
-template <int NB, int R, int MAXJ, int VPT>
+template <int NB, int R, int MAXJ, int VPT, int MAXT, bool GLOBAL>
 __global__ void __launch_bounds__(512, 1) eig_tri_kernel(EigArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = a.n;
   const int ld = n | 1;
   const int tid = threadIdx.x;
-  float* A = reinterpret_cast<float*>(smem_raw);
+  // A and the scratch area in shared memory, or (large buffers) in the
+  // global workspace a.work
+  float* A = GLOBAL ? reinterpret_cast<float*>(a.work) : reinterpret_cast<float*>(smem_raw);
+  unsigned char* scr = GLOBAL ? reinterpret_cast<unsigned char*>(a.work) + tri_al16((size_t)n * ld * 4)
+                              : smem_raw + tri_al16((size_t)n * ld * 4);
+  unsigned char* small = GLOBAL ? smem_raw : scr + tri_scratch_bytes(n, NB);
   __shared__ float s_max;
   eig_load<float>(a, A, ld, n, n);
   if (tid == 0) s_max = 0.f;
@@ -334,34 +339,37 @@ __global__ void __launch_bounds__(512, 1) eig_tri_kernel(EigArgs a) {
   const float inv = (smax > 0.f) ? 1.f / smax : 1.f;
   for (int idx = tid; idx < n * ld; idx += blockDim.x) A[idx] *= inv;
   __syncthreads();
-  tri_eig_shrink<NB, R, MAXJ, VPT>(a, A, ld, n, (smax > 0.f) ? (double)smax : 1.0,
-                              smem_raw + tri_al16((size_t)n * ld * 4));
+  tri_eig_shrink<NB, R, MAXJ, VPT, MAXT>(a, A, ld, n, (smax > 0.f) ? (double)smax : 1.0, scr, small);
 }
 
-template <int NB, int R, int MAXJ, int VPT>
+template <int NB, int R, int MAXJ, int VPT, int MAXT, bool GLOBAL>
 cudaError_t launch_tri(const EigArgs& a, size_t smem, cudaStream_t st) {
   static size_t attr_set = 0;
   if (smem > attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(eig_tri_kernel<NB, R, MAXJ, VPT>,
+    cudaError_t e = cudaFuncSetAttribute(eig_tri_kernel<NB, R, MAXJ, VPT, MAXT, GLOBAL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = smem;
   }
-  eig_tri_kernel<NB, R, MAXJ, VPT><<<1, 512, smem, st>>>(a);
+  eig_tri_kernel<NB, R, MAXJ, VPT, MAXT, GLOBAL><<<1, 512, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 // Whether a reduction of n rows takes the tridiagonal eigensolve: full
-// buffers whose solve fits in shared memory (n <= 206); flushes of a partial
-// buffer keep Jacobi. 1: n <= 128, 2 and 3: up to 208 rows (LU batches of
-// 16 or 8 vectors for the fallback path).
+// buffers only (flushes of a partial buffer keep Jacobi). 1: n <= 128 in
+// shared memory; 2, 3: up to 206 rows in shared memory (LU batches of 16 or 8
+// vectors for the fallback path); 4: up to 512 rows with A and the scratch
+// area in a global workspace of tri_global_bytes(n, 16) bytes.
 int tri_config(int n, int ell) {
   if (n != 2 * ell || n < 4) return 0;
   if (n <= 128 && tri_smem_bytes(n, 32) <= 226 * 1024) return 1;
   if (n <= 208 && tri_smem_bytes(n, 16) <= 226 * 1024) return 2;
   if (n <= 208 && tri_smem_bytes(n, 8) <= 226 * 1024) return 3;
+  if (n <= 512) return 4;
   return 0;
 }
+
+size_t tri_global_workspace(int n) { return tri_global_bytes(n, 16); }
 
 size_t eig_fast_smem(int np) {
   const int ld = (np + 3) & ~3;
@@ -391,11 +399,13 @@ cudaError_t launch_fast(const EigArgs& a, size_t smem, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_eig_shrink(const EigArgs& a, cudaStream_t st) {
   const int np = a.n + (a.n & 1);
-  if (sizeof(T) == 4 && a.work == nullptr && a.use_tri) {
+  if (sizeof(T) == 4 && a.use_tri) {
     const int cfg = tri_config(a.n, a.ell);
-    if (cfg == 1) return launch_tri<32, 8, 16, 1>(a, tri_smem_bytes(a.n, 32), st);
-    if (cfg == 2) return launch_tri<16, 8, 26, 2>(a, tri_smem_bytes(a.n, 16), st);
-    if (cfg == 3) return launch_tri<8, 8, 26, 2>(a, tri_smem_bytes(a.n, 8), st);
+    if (cfg == 1) return launch_tri<32, 8, 16, 1, 4, false>(a, tri_smem_bytes(a.n, 32), st);
+    if (cfg == 2) return launch_tri<16, 8, 26, 2, 7, false>(a, tri_smem_bytes(a.n, 16), st);
+    if (cfg == 3) return launch_tri<8, 8, 26, 2, 7, false>(a, tri_smem_bytes(a.n, 8), st);
+    if (cfg == 4 && a.work != nullptr && a.work_bytes >= tri_global_bytes(a.n, 16))
+      return launch_tri<16, 16, 32, 2, 16, true>(a, tri_small_bytes(a.n), st);
   }
   if (sizeof(T) == 4 && a.work == nullptr && np <= 224 && eig_fast_smem(np) <= 226 * 1024) {
     const size_t smem = eig_fast_smem(np);

@@ -39,9 +39,7 @@
 
 namespace fdk {
 
-constexpr int TRI_MAXN = 256;
-constexpr int TRI_MAXT = TRI_MAXN / 32;  // column chunks per lane in step 1
-constexpr int TRI_KR = 16;               // row slots per warp in step 1 (n - 1 <= 16 * warps)
+constexpr int TRI_KR = 16;  // row slots per warp and batch in step 1
 
 __host__ __device__ constexpr size_t tri_al16(size_t b) { return (b + 15) / 16 * 16; }
 // offset (floats) of reflector s (length n-1-s) in the packed store
@@ -64,10 +62,19 @@ __host__ __device__ constexpr size_t tri_scratch_bytes(int n, int NB) {
 __host__ __device__ constexpr size_t tri_fv_floats(int n) {
   return 64 + 5 * (size_t)((n + 7) & ~7) + 4 * (size_t)n;
 }
+// the small-vector region (always in shared memory)
+__host__ __device__ constexpr size_t tri_small_bytes(int n) {
+  return tri_al16((size_t)n * 16)              // mu, mup
+         + tri_al16(tri_fv_floats(n) * 4)      // small vectors
+         + tri_al16((size_t)(2 * n + 16) * 4); // rrank pos
+}
 __host__ __device__ constexpr size_t tri_rest_bytes(int n, int NB) {
-  return tri_scratch_bytes(n, NB) + tri_al16((size_t)n * 16)  // mu, mup
-         + tri_al16(tri_fv_floats(n) * 4)                      // small vectors
-         + tri_al16((size_t)(2 * n + 16) * 4);                 // rrank pos
+  return tri_scratch_bytes(n, NB) + tri_small_bytes(n);
+}
+// Global-memory workspace of the solve when A and the scratch area do not fit
+// in shared memory (n x (n|1) floats, then the scratch area).
+__host__ __device__ constexpr size_t tri_global_bytes(int n, int NB) {
+  return tri_al16((size_t)n * (size_t)(n | 1) * 4) + tri_scratch_bytes(n, NB);
 }
 // Shared-memory bytes of the whole solve for n rows (A with stride n | 1).
 __host__ __device__ constexpr size_t tri_smem_bytes(int n, int NB) {
@@ -96,8 +103,9 @@ __device__ __forceinline__ float tri_sum_parts(const float* p, int nw) {
   return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 }
 
-static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, float* xb,
-                                  float* vb0, float* vb1, float* qb, float* pb, float* red) {
+template <int MAXT>  // column chunks of 32 per row: n - 1 <= 32 MAXT
+__device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, float* xb, float* vb0,
+                           float* vb1, float* qb, float* pb, float* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   float* kpart = red;       // per-warp parts of K = v^T p
@@ -143,9 +151,9 @@ static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, f
     {
       const bool upd = s > 0;
       const int tmax = (m + 31) >> 5;
-      float wc[TRI_MAXT], vc[TRI_MAXT], qc[TRI_MAXT];
+      float wc[MAXT], vc[MAXT], qc[MAXT];
 #pragma unroll
-      for (int t = 0; t < TRI_MAXT; ++t) {
+      for (int t = 0; t < MAXT; ++t) {
         const int c = lane + 32 * t;
         wc[t] = vc[t] = qc[t] = 0.f;
         if (c < m) {
@@ -156,56 +164,60 @@ static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, f
           }
         }
       }
-      float acc[TRI_KR];
+      float kp = 0.f;
+      // rows r = warp + k nw in batches of TRI_KR slots (one batch unless a
+      // warp owns more than TRI_KR rows)
+      for (int kb = 0; warp + kb * nw < m; kb += TRI_KR) {
+        float acc[TRI_KR];
 #pragma unroll
-      for (int k = 0; k < TRI_KR; ++k) acc[k] = 0.f;
+        for (int k = 0; k < TRI_KR; ++k) acc[k] = 0.f;
 #pragma unroll
-      for (int k0 = 0; k0 < TRI_KR; k0 += 4) {
-        if (warp + k0 * nw < m) {  // uniform across the warp
+        for (int k0 = 0; k0 < TRI_KR; k0 += 4) {
+          if (warp + (kb + k0) * nw < m) {  // uniform across the warp
 #pragma unroll
-          for (int k = k0; k < k0 + 4; ++k) {
-            const int r = warp + k * nw;
-            const bool rv = r < m;
-            const int rr = rv ? r : m - 1;
-            float* row = A + (size_t)(s + 1 + rr) * ld + (s + 1);
-            const float vr = (upd && rv) ? vprv[rr + 1] : 0.f;
-            const float qr = (upd && rv) ? qb[rr + 1] : 0.f;
+            for (int k = k0; k < k0 + 4; ++k) {
+              const int r = warp + (kb + k) * nw;
+              const bool rv = r < m;
+              const int rr = rv ? r : m - 1;
+              float* row = A + (size_t)(s + 1 + rr) * ld + (s + 1);
+              const float vr = (upd && rv) ? vprv[rr + 1] : 0.f;
+              const float qr = (upd && rv) ? qb[rr + 1] : 0.f;
 #pragma unroll
-            for (int t = 0; t < TRI_MAXT; ++t) {
-              if (t < tmax) {
-                const int c = lane + 32 * t;
-                if (c < m) {
-                  float a = row[c];
-                  if (upd) {
-                    a = fmaf(-vr, qc[t], fmaf(-qr, vc[t], a));
-                    if (rv) row[c] = a;
+              for (int t = 0; t < MAXT; ++t) {
+                if (t < tmax) {
+                  const int c = lane + 32 * t;
+                  if (c < m) {
+                    float a = row[c];
+                    if (upd) {
+                      a = fmaf(-vr, qc[t], fmaf(-qr, vc[t], a));
+                      if (rv) row[c] = a;
+                    }
+                    acc[k] = fmaf(a, wc[t], acc[k]);
                   }
-                  acc[k] = fmaf(a, wc[t], acc[k]);
                 }
               }
             }
           }
         }
-      }
-      // butterfly over the 16 slots: lane l ends with slot (l >> 1) summed over all lanes
-      const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-      float l1[8], l2[4], l3[2];
+        // butterfly over the 16 slots: lane l ends with slot (l >> 1) summed over all lanes
+        const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+        float l1[8], l2[4], l3[2];
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        l1[q] = (b4 ? acc[8 + q] : acc[q]) + __shfl_xor_sync(0xffffffffu, b4 ? acc[q] : acc[8 + q], 16);
+        for (int q = 0; q < 8; ++q)
+          l1[q] = (b4 ? acc[8 + q] : acc[q]) + __shfl_xor_sync(0xffffffffu, b4 ? acc[q] : acc[8 + q], 16);
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        l2[q] = (b3 ? l1[4 + q] : l1[q]) + __shfl_xor_sync(0xffffffffu, b3 ? l1[q] : l1[4 + q], 8);
+        for (int q = 0; q < 4; ++q)
+          l2[q] = (b3 ? l1[4 + q] : l1[q]) + __shfl_xor_sync(0xffffffffu, b3 ? l1[q] : l1[4 + q], 8);
 #pragma unroll
-      for (int q = 0; q < 2; ++q)
-        l3[q] = (b2 ? l2[2 + q] : l2[q]) + __shfl_xor_sync(0xffffffffu, b2 ? l2[q] : l2[2 + q], 4);
-      float tot = (b1 ? l3[1] : l3[0]) + __shfl_xor_sync(0xffffffffu, b1 ? l3[0] : l3[1], 2);
-      tot += __shfl_xor_sync(0xffffffffu, tot, 1);
-      const int r = warp + (lane >> 1) * nw;
-      float kp = 0.f;
-      if (!(lane & 1) && r < m) {
-        pb[r] = tot;
-        kp = ((r == 0) ? (x0 - alpha) : xb[r]) * scale * tot;
+        for (int q = 0; q < 2; ++q)
+          l3[q] = (b2 ? l2[2 + q] : l2[q]) + __shfl_xor_sync(0xffffffffu, b2 ? l2[q] : l2[2 + q], 4);
+        float tot = (b1 ? l3[1] : l3[0]) + __shfl_xor_sync(0xffffffffu, b1 ? l3[0] : l3[1], 2);
+        tot += __shfl_xor_sync(0xffffffffu, tot, 1);
+        const int r = warp + (kb + (lane >> 1)) * nw;
+        if (!(lane & 1) && r < m) {
+          pb[r] = tot;
+          kp = fmaf(((r == 0) ? (x0 - alpha) : xb[r]) * scale, tot, kp);
+        }
       }
       kp = warp_sum(kp);
       if (lane == 0) kpart[warp] = kp;
@@ -1218,16 +1230,17 @@ __device__ void tri_back_write(const EigArgs& a, const float* V, int n, const fl
 // ---------------------------------------------------------------------------
 // The whole eigensolve + ReduceRank shrink + rotate-matrix write for a full
 // buffer of n = 2*ell rows whose Gram is in A (n x ld, scaled by 1/smax).
-// NB: vectors per fallback inverse-iteration batch; R, MAXJ: step-5 layout
-// (n <= R * MAXJ, R * min(count, nt / R) <= nt).
+// NB: vectors per fallback inverse-iteration batch; R, MAXJ, VPT: step-5
+// layout (n <= R * MAXJ); MAXT: step-1 column chunks (n - 1 <= 32 MAXT).
+// scr_raw: tri_scratch_bytes(n, NB) bytes; small: tri_small_bytes(n) bytes of
+// shared memory. A and scr_raw may be in shared or in global memory.
 // ---------------------------------------------------------------------------
-template <int NB, int R, int MAXJ, int VPT>
+template <int NB, int R, int MAXJ, int VPT, int MAXT>
 __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double smax,
-                               unsigned char* rest) {
+                               unsigned char* scr_raw, unsigned char* small) {
   constexpr int TRI_CU = (R * MAXJ / 2 + 31) / 32;  // retained vectors <= n / 2 <= 32 TRI_CU
   const int tid = threadIdx.x, nt = blockDim.x;
-  unsigned char* scr_raw = rest;
-  double* mu = reinterpret_cast<double*>(rest + tri_scratch_bytes(n, NB));
+  double* mu = reinterpret_cast<double*>(small);
   double* mup = mu + n;
   float* fv = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(mu) + tri_al16((size_t)n * 16));
   const int np8 = (n + 7) & ~7;
@@ -1248,7 +1261,7 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
   __shared__ int s_count, s_ok;
   __shared__ double s_dsum, s_dlast;
 
-  tri_reduce(A, ld, n, d, e, xb, vb0, vb1, qb, pb, red);
+  tri_reduce<MAXT>(A, ld, n, d, e, xb, vb0, vb1, qb, pb, red);
   tri_bisect(d, e, e2, n, lam, &s_tnorm, reinterpret_cast<int*>(scr_raw));
   {
     // eigenvalues at or below the bisection's resolution (2 eps lambda_1)
