@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
     ap.add_argument("--cpu-sample-rows", type=int, default=0)
     ap.add_argument("--count", type=int, help="batched workload: number of sketches")
+    ap.add_argument("--shards", type=int, default=16,
+                    help="single stream: also time P contiguous shards sketched concurrently "
+                         "and merged pairwise (0 = skip)")
     return ap.parse_args()
 
 
@@ -603,6 +606,40 @@ def main():
         plain = {"value": w["n"] / (pms / 1e3), "unit": "rows/s", "cov_err": sp.cov_err(A)}
         sp.close()
 
+    # sharded: P contiguous shards, one handle and CUDA stream each (their
+    # reductions run concurrently on different SMs), then fd_merge pairwise.
+    # A different FD run from the sequential stream, reported beside it.
+    sharded = None
+    if args.shards and args.shards > 1 and rank == 0:
+        P = args.shards
+        cuts = [w["n"] * i // P for i in range(P + 1)]
+        streams = [torch.cuda.Stream() for _ in range(P)]
+        shs = [fd.FDSketch(w["d"], w["ell"], w["variant"], w["alpha"], w["prec"], stream=st)
+               for st in streams]
+
+        def sharded_run():
+            for h, a, b in zip(shs, cuts[:-1], cuts[1:]):
+                h.reset()
+                h.append(A[a:b])
+            root = fd.merge_tree(shs)
+            root.sketch(out=B)
+            return root
+
+        sharded_run()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = max(1, args.steps)
+        for _ in range(reps):
+            root = sharded_run()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        sharded = {"shards": P, "value": w["n"] / dt, "unit": "rows/s",
+                   "cov_err": root.cov_err(A),
+                   "timing": "host wall clock around the whole run (appends, merges, sketch)",
+                   "note": "contiguous shards sketched concurrently, merged pairwise with fd_merge"}
+        for h in shs:
+            h.close()
+
     if rank != 0:
         sk.close()
         return 0
@@ -640,7 +677,7 @@ def main():
                    "l2": "input larger than L2 (no flush needed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "cov_err": cov, "reductions_per_step": st["reductions"],
-        "plain_fp32": plain,
+        "plain_fp32": plain, "sharded": sharded,
         "roofline": roofline, "kernels": kshare,
         "gpu_launches": int(launches + 2 * args.steps),
         "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,

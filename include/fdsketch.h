@@ -120,6 +120,20 @@ int fd_append(fd_handle h, const void* rows, int64_t n, int64_t ld, int32_t dtyp
  * output the call synchronises the stream. */
 int fd_sketch(fd_handle h, void* out, int32_t dtype, int32_t out_on_device);
 
+/* Merge two sketches of the same width d. The paper states the problem for
+ * streams that may be distributed (Sec. 1). src's current sketch (as
+ * fd_sketch returns it, taken on a copy: src is unchanged) is appended to dst
+ * as ordinary stream rows, up to its last nonzero row, so dst becomes a sketch
+ * of the union of both streams. Every later reduction of dst is an ordinary
+ * one, so Lemma 1 (Sec. 3.1), applied to both streams, gives
+ * 0 <= x^T (A^T A - B^T B) x <= (sum of all deltas) for the union.
+ * dst's counters take src's: ||A||_F^2 counts src's rows instead of the
+ * appended sketch rows; src's deltas, removed mass, reductions and row count
+ * are added. ell, variant and precision may differ (dst's apply).
+ * Synchronises both handles' streams. Errors: FD_EINVAL (null, dst == src,
+ * different d), FD_ECUDA. */
+int fd_merge(fd_handle dst, fd_handle src);
+
 /* cov-err(A, B) = ||A^T A - B^T B||_2 / ||A||_F^2 (Sec. 1.1) for the handle's
  * current sketch B (as fd_sketch returns it) and the n x d matrix A, with
  * ||.||_2 = max |eigenvalue| (Sec. 1.1, the maximum of |(||Ax||^2 - ||Bx||^2)|

@@ -279,6 +279,38 @@ class FDOracle:
         return B, info
 
 
+    def merge(self, other: "FDOracle"):
+        """Fold ``other``'s stream into this sketch (merge of two sketches).
+
+        The paper states the problem for streams that may be distributed
+        (Sec. 1); a merge takes ``other``'s sketch (``other.sketch()``,
+        non-destructive) and appends its rows to this stream, so that every
+        later reduction treats them as ordinary rows. By the per-step bound
+        of Lemma 1 (Sec. 3.1), applied to this stream and to ``other``'s,
+        the result keeps 0 <= x^T (A^T A - B^T B) x <= (sum of all deltas)
+        for the union of both streams. The counters carry ``other``'s:
+        ``normA2`` counts ``other``'s rows instead of the appended sketch
+        rows; ``other``'s deltas, removed mass, reductions and row count are
+        added. Only the retained (nonzero) rows are appended: they come
+        first in the sketch, and zero rows carry no mass but would take
+        buffer slots.
+        """
+        if other.d != self.d:
+            raise ValueError("row width differs")
+        if other is self:
+            raise ValueError("cannot merge a sketch into itself")
+        B, info = other.sketch()
+        nz = np.flatnonzero(np.any(B != 0.0, axis=1))
+        rows = B[: (int(nz[-1]) + 1 if nz.size else 0)]
+        na2, ns = self.normA2, self.n_seen
+        self.append(rows)
+        self.normA2 = na2 + info["normA2"]
+        self.n_seen = ns + info["n_seen"]
+        self.sum_delta += info["sum_delta"]
+        self.removed += info["removed"]
+        self.reductions += info["reductions"]
+
+
 def fd_sketch(A, ell: int, variant: str = "fd", alpha: float = 1.0,
               mode: str = "buffered", record: bool = False):
     """Run the whole stream ``A`` (rows in order) and return ``(B, info)``.

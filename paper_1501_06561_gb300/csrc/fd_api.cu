@@ -99,6 +99,8 @@ struct fd_state {
   cudaEvent_t stage_ev[2] = {nullptr, nullptr};
   int stage_next = 0;
   DevCounters* hctr = nullptr;  // pinned copy for fd_stats
+  int* dint = nullptr;          // device int (merge: rows of the sketch)
+  int* hint = nullptr;          // pinned copy
 
   TcCtx* tc = nullptr;    // tensor-core planes (FD_PREC_BF16X3)
   int max_sweeps = 30;
@@ -173,6 +175,8 @@ static void free_state(fd_state* h) {
   cudaFree(h->sig2);
   cudaFree(h->sigp2);
   if (h->hctr) cudaFreeHost(h->hctr);
+  cudaFree(h->dint);
+  if (h->hint) cudaFreeHost(h->hint);
   if (h->tc) tc_destroy(h->tc);
   delete h;
 }
@@ -245,6 +249,7 @@ extern "C" int fd_create(int64_t d, int32_t ell, int32_t variant, double alpha, 
   FD_ALLOC(h->ctr, sizeof(DevCounters));
   FD_ALLOC(h->ctr_flush, sizeof(DevCounters));
   FD_ALLOC(h->rownorm, (size_t)FD_MAX_BUFFER_ROWS * 8);
+  FD_ALLOC(h->dint, 16);
   FD_ALLOC(h->sig2, (size_t)FD_MAX_BUFFER_ROWS * 8);
   FD_ALLOC(h->sigp2, (size_t)FD_MAX_BUFFER_ROWS * 8);
 #undef FD_ALLOC
@@ -259,6 +264,8 @@ extern "C" int fd_create(int64_t d, int32_t ell, int32_t variant, double alpha, 
   }
   e = cudaMallocHost(reinterpret_cast<void**>(&h->hctr), 2 * sizeof(DevCounters));
   if (e != cudaSuccess) return fail(e, "cudaMallocHost counters");
+  e = cudaMallocHost(reinterpret_cast<void**>(&h->hint), 16);
+  if (e != cudaSuccess) return fail(e, "cudaMallocHost hint");
   e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return fail(e, "cudaStreamSynchronize");
   *out = h;
@@ -439,6 +446,29 @@ extern "C" int fd_sketch(fd_handle h, void* out, int32_t dtype, int32_t out_on_d
   FD_CK(cudaMemcpyAsync(out, h->outdev, (size_t)h->ell * h->d * (dst_f64 ? 8 : 4),
                         cudaMemcpyDeviceToHost, h->st));
   FD_CK(cudaStreamSynchronize(h->st));
+  return FD_OK;
+}
+
+// Merge: src's sketch rows become stream rows of dst (see fdsketch.h).
+extern "C" int fd_merge(fd_handle dst, fd_handle src) {
+  if (!dst || !src || dst == src || dst->d != src->d) return FD_EINVAL;
+  const int32_t dt = (dst->prec == FD_PREC_FP64) ? FD_F64 : FD_F32;
+  int rc = fd_sketch(src, src->outdev, dt, 1);  // on a copy: src is unchanged
+  if (rc != FD_OK) return rc;
+  FD_CK(launch_last_nonzero_row(src->outdev, dt == FD_F64, src->d, src->ell, src->d, src->dint,
+                                src->st));
+  FD_CK(cudaMemcpyAsync(src->hint, src->dint, sizeof(int), cudaMemcpyDeviceToHost, src->st));
+  FD_CK(cudaStreamSynchronize(src->st));
+  const int rows = *src->hint;
+  dst->flushed = false;
+  if (rows > 0) {
+    rc = append_device(dst, reinterpret_cast<const char*>(src->outdev), rows, src->d, dt);
+    if (rc != FD_OK) return rc;
+  }
+  FD_CK(launch_merge_counters(dst->ctr, src->ctr_flush, dst->st));
+  dst->n_seen += src->n_seen - rows;
+  // src's buffers feed dst's stream: finish before src can reuse them
+  FD_CK(cudaStreamSynchronize(dst->st));
   return FD_OK;
 }
 

@@ -80,6 +80,11 @@ cudaError_t launch_convert_out(const void* src, int src_f64, int64_t lds, int ro
 cudaError_t launch_norm_b2(const void* src, int src_f64, int64_t lds, int rows,
                            int64_t d, DevCounters* ctr, cudaStream_t st);
 
+cudaError_t launch_last_nonzero_row(const void* src, int src_f64, int64_t lds, int rows, int64_t d,
+                                    int* out, cudaStream_t st);
+
+cudaError_t launch_merge_counters(DevCounters* dst, const DevCounters* src, cudaStream_t st);
+
 // --- tensor-core path (fd_tc.cu) ---------------------------------------------
 struct TcPlanes;  // opaque, defined in fd_tc.cu
 int tc_available();

@@ -553,6 +553,50 @@ cudaError_t launch_norm_b2(const void* src, int src_f64, int64_t lds, int rows, 
   return cudaGetLastError();
 }
 
+// Rows of a sketch up to its last nonzero one (1 + index, 0 if all zero):
+// one warp per row, block-wide maximum.
+__global__ void last_nonzero_row_kernel(const void* __restrict__ src, int src_f64, int64_t lds,
+                                        int rows, int64_t d, int* out) {
+  __shared__ int s_last;
+  if (threadIdx.x == 0) s_last = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; r < rows; r += nw) {
+    int nz = 0;
+    for (int64_t k = lane; k < d && !nz; k += 32) {
+      const double v = src_f64 ? reinterpret_cast<const double*>(src)[(int64_t)r * lds + k]
+                               : (double)reinterpret_cast<const float*>(src)[(int64_t)r * lds + k];
+      nz = (v != 0.0);
+    }
+    if (__any_sync(0xffffffffu, nz) && lane == 0) atomicMax(&s_last, r + 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *out = s_last;
+}
+
+cudaError_t launch_last_nonzero_row(const void* src, int src_f64, int64_t lds, int rows, int64_t d,
+                                    int* out, cudaStream_t st) {
+  last_nonzero_row_kernel<<<1, 256, 0, st>>>(src, src_f64, lds, rows, d, out);
+  return cudaGetLastError();
+}
+
+// Counters of a merge: dst takes src's stream mass in place of the appended
+// sketch rows' mass (ingest already added ||B_src||_F^2), and src's deltas,
+// removed mass and reductions (src: the counters of its latest sketch).
+__global__ void merge_counters_kernel(DevCounters* dst, const DevCounters* src) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    dst->norm_a2 += src->norm_a2 - src->norm_b2;
+    dst->sum_delta += src->sum_delta;
+    dst->removed += src->removed;
+    dst->reductions += src->reductions;
+  }
+}
+
+cudaError_t launch_merge_counters(DevCounters* dst, const DevCounters* src, cudaStream_t st) {
+  merge_counters_kernel<<<1, 32, 0, st>>>(dst, src);
+  return cudaGetLastError();
+}
+
 }  // namespace fdk
 
 namespace fdk {

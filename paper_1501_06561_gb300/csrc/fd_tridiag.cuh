@@ -653,18 +653,18 @@ __device__ bool tri_cholqr(float* Zt, int ldz, int n, int count, float* C, int l
 
 // ---------------------------------------------------------------------------
 // Fallback of steps 3-4: inverse iteration from a random start for vectors
-// c0 .. min(c0+NB, cend)-1 (thread t < NB takes vector c0 + t): eigenvalue
-// lam[pos[c]], (T - lambda I) z = z solved three times by LU with partial
-// pivoting. scr holds NB interleaved copies of the four LU bands, piv NB x n
+// list[c0 .. min(c0+NB, cend)-1] (c0 + t itself without a list; thread
+// t < NB takes one): eigenvalue lam[pos[c]], (T - lambda I) z = z solved
+// `reps` times by LU with partial pivoting. scr holds NB interleaved copies of the four LU bands, piv NB x n
 // pivot flags.
 // ---------------------------------------------------------------------------
 template <int NB>
 __device__ void tri_invit_batch(float* Zt, int ldz, int n, const float* d, const float* e,
-                                const float* lam, const int* pos, int c0, int cend, float tnorm,
-                                float* scr, unsigned char* piv) {
+                                const float* lam, const int* pos, const int* list, int c0,
+                                int cend, float tnorm, float* scr, unsigned char* piv, int reps) {
   const int t = threadIdx.x;
-  const int c = c0 + t;
-  if (t >= NB || c >= cend) return;
+  if (t >= NB || c0 + t >= cend) return;
+  const int c = list ? list[c0 + t] : c0 + t;
   float* dd = scr;
   float* du = scr + (size_t)NB * n;
   float* du2 = scr + (size_t)2 * NB * n;
@@ -719,7 +719,7 @@ __device__ void tri_invit_batch(float* Zt, int ldz, int n, const float* d, const
     h ^= h >> 13;
     Z(i) = 1.f + 0.25f * ((float)(h & 0xffff) / 65536.f - 0.5f);
   }
-  for (int rep = 0; rep < 3; ++rep) {
+  for (int rep = 0; rep < reps; ++rep) {
     for (int i = 0; i + 1 < n; ++i) {
       if (!PV(i)) {
         Z(i + 1) = Z(i + 1) - DL(i) * Z(i);
@@ -759,149 +759,28 @@ __device__ void tri_invit_batch(float* Zt, int ldz, int n, const float* d, const
 #undef Z
 }
 
-// Fallback of steps 3-4 for clusters (LAPACK-style inverse iteration): the
-// retained positions are ordered by eigenvalue and split into clusters where
-// neighbours are closer than gtol. The members of each cluster of two or more
-// are recomputed one after another by one thread: LU with partial pivoting of
-// T - (lambda + k * shift) I (k = index in the cluster), then five steps of
-// "solve, orthogonalise against the members already done (modified
-// Gram-Schmidt), normalise". Clusters run in parallel, NB at a time. Single
-// vectors keep their twisted solution. ord: count ints; cbeg: 2 ints per
-// cluster (at most count).
-template <int NB>
-__device__ void tri_invit_clusters(float* Zt, int ldz, int n, const float* d, const float* e,
-                                   const float* lam, const int* pos, int count, float tnorm,
-                                   float gtol, float* scr, unsigned char* piv, int* ord,
-                                   int* cbeg) {
-  const int tid = threadIdx.x;
-  __shared__ int s_ncl;
-  if (tid == 0) {
-    // order by position (positions are sorted by eigenvalue, descending)
+// Members of clusters for the fallback: the retained positions ordered by
+// eigenvalue are split where neighbours are more than gtol apart; the members
+// of every group of two or more go to list (thread 0; returns their number
+// through *nlist, shared).
+static __device__ void tri_cluster_members(const float* lam, const int* pos, int n, int count,
+                                           float gtol, int* ord, int* list, int* nlist) {
+  if (threadIdx.x == 0) {
     int k = 0;
     for (int q = 0; q < n && k < count; ++q)
       for (int r = 0; r < count; ++r)
         if (pos[r] == q) ord[k++] = r;
-    int ncl = 0;
+    int nl = 0;
     for (int a = 0; a < count;) {
       int b = a + 1;
       while (b < count && lam[pos[ord[b - 1]]] - lam[pos[ord[b]]] <= gtol) ++b;
-      if (b - a >= 2) cbeg[2 * ncl] = a, cbeg[2 * ncl + 1] = b, ++ncl;
+      if (b - a >= 2)
+        for (int j = a; j < b; ++j) list[nl++] = ord[j];
       a = b;
     }
-    s_ncl = ncl;
+    *nlist = nl;
   }
   __syncthreads();
-  const int ncl = s_ncl;
-  const float eps = 1.1920929e-07f;
-  const float tiny = eps * fmaxf(tnorm, 1e-30f);
-  const float shift = 16.f * eps * fmaxf(tnorm, 1e-30f);
-  for (int c0 = 0; c0 < ncl; c0 += NB) {
-    const int t = tid, ci = c0 + t;
-    if (t < NB && ci < ncl) {
-      float* dd = scr;
-      float* du = scr + (size_t)NB * n;
-      float* du2 = scr + (size_t)2 * NB * n;
-      float* dl = scr + (size_t)3 * NB * n;
-#define DD(i) dd[(size_t)(i) * NB + t]
-#define DU(i) du[(size_t)(i) * NB + t]
-#define DU2(i) du2[(size_t)(i) * NB + t]
-#define DL(i) dl[(size_t)(i) * NB + t]
-#define PV(i) piv[(size_t)(i) * NB + t]
-      const int a = cbeg[2 * ci], b = cbeg[2 * ci + 1];
-      for (int mi = a; mi < b; ++mi) {
-        const int c = ord[mi];
-        float* z = Zt + c;
-        const float lmb = lam[pos[c]] + (float)(mi - a) * shift;
-        for (int i = 0; i < n; ++i) {
-          DD(i) = d[i] - lmb;
-          if (i < n - 1) {
-            DU(i) = e[i];
-            DL(i) = e[i];
-            DU2(i) = 0.f;
-          }
-        }
-        for (int i = 0; i + 1 < n; ++i) {
-          const float di = DD(i), li = DL(i);
-          if (fabsf(di) >= fabsf(li)) {
-            const float dv = (di == 0.f) ? tiny : di;
-            DD(i) = dv;
-            const float f = li / dv;
-            DL(i) = f;
-            DD(i + 1) = DD(i + 1) - f * DU(i);
-            PV(i) = 0;
-          } else {
-            const float f = di / li;
-            DD(i) = li;
-            DL(i) = f;
-            const float tmp = DU(i);
-            const float dn = DD(i + 1);
-            DU(i) = dn;
-            DD(i + 1) = tmp - f * dn;
-            if (i + 2 < n) {
-              DU2(i) = DU(i + 1);
-              DU(i + 1) = -f * DU(i + 1);
-            }
-            PV(i) = 1;
-          }
-        }
-        if (DD(n - 1) == 0.f) DD(n - 1) = tiny;
-        for (int i = 0; i < n; ++i) {  // start: ones with a deterministic perturbation
-          unsigned h = (unsigned)(i * 2654435761u) ^ (unsigned)(c * 40503u + 0x9e3779b9u);
-          h ^= h >> 15;
-          h *= 2246822519u;
-          h ^= h >> 13;
-          z[(size_t)i * ldz] = 1.f + 0.25f * ((float)(h & 0xffff) / 65536.f - 0.5f);
-        }
-        for (int rep = 0; rep < 5; ++rep) {
-          for (int i = 0; i + 1 < n; ++i) {
-            const float zi = z[(size_t)i * ldz], zj = z[(size_t)(i + 1) * ldz];
-            if (!PV(i)) {
-              z[(size_t)(i + 1) * ldz] = zj - DL(i) * zi;
-            } else {
-              z[(size_t)i * ldz] = zj;
-              z[(size_t)(i + 1) * ldz] = zi - DL(i) * zj;
-            }
-          }
-          float x2 = 0.f, x1 = 0.f;
-          for (int i = n - 1; i >= 0; --i) {
-            float v = z[(size_t)i * ldz];
-            if (i + 1 < n) v -= DU(i) * x1;
-            if (i + 2 < n) v -= DU2(i) * x2;
-            v /= DD(i);
-            z[(size_t)i * ldz] = v;
-            x2 = x1;
-            x1 = v;
-          }
-          float mx = 0.f;
-          for (int i = 0; i < n; ++i) mx = fmaxf(mx, fabsf(z[(size_t)i * ldz]));
-          const float inv = (mx > 0.f) ? 1.f / mx : 1.f;
-          for (int i = 0; i < n; ++i) z[(size_t)i * ldz] *= inv;
-          for (int pj = a; pj < mi; ++pj) {  // against the members already done
-            const float* y = Zt + ord[pj];
-            float h0 = 0.f, h1 = 0.f;
-            int i = 0;
-            for (; i + 1 < n; i += 2) {
-              h0 = fmaf(z[(size_t)i * ldz], y[(size_t)i * ldz], h0);
-              h1 = fmaf(z[(size_t)(i + 1) * ldz], y[(size_t)(i + 1) * ldz], h1);
-            }
-            if (i < n) h0 = fmaf(z[(size_t)i * ldz], y[(size_t)i * ldz], h0);
-            const float hh = h0 + h1;
-            for (int k = 0; k < n; ++k) z[(size_t)k * ldz] = fmaf(-hh, y[(size_t)k * ldz], z[(size_t)k * ldz]);
-          }
-          float s2 = 0.f;
-          for (int i = 0; i < n; ++i) s2 = fmaf(z[(size_t)i * ldz], z[(size_t)i * ldz], s2);
-          const float r = 1.f / sqrtf(fmaxf(s2, 1e-30f));
-          for (int i = 0; i < n; ++i) z[(size_t)i * ldz] *= r;
-        }
-      }
-#undef DD
-#undef DU
-#undef DU2
-#undef DL
-#undef PV
-    }
-    __syncthreads();
-  }
 }
 
 __device__ __forceinline__ float tri_block_sum(float v, float* red) {
@@ -1294,26 +1173,37 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
     ok = tri_cholqr<TRI_CU>(Zt, ldz, n, count, C, ldc, dinv, 0.25f);
   }
   if (!ok) {
-    // clusters recomputed with reorthogonalisation, then Cholesky-QR again;
-    // classical Gram-Schmidt (twice) if that still fails
+    // Vectors of close eigenvalues came out nearly dependent. Within a window
+    // of a few eps ||T|| any orthonormal basis of the invariant subspace is
+    // as good, so the members of such clusters are replaced by one
+    // inverse-iteration solve from a random start each (generic, independent
+    // combinations inside the subspace); then Cholesky-QR again. If a twisted
+    // vector failed, or that still fails, every vector is recomputed that way
+    // and orthonormalised by classical Gram-Schmidt (twice).
+    __shared__ int s_nl;
     __syncthreads();
     float* scr = reinterpret_cast<float*>(scr_raw);
     unsigned char* piv = scr_raw + tri_al16((size_t)NB * n * 16);
-    if (s_ok) {
-      tri_invit_clusters<NB>(Zt, ldz, n, d, e, lam, pos, count, tnorm, 1e-4f * tnorm, scr, piv,
-                             reinterpret_cast<int*>(pb), reinterpret_cast<int*>(pb) + (count + 1));
-    } else {
-      for (int c0 = 0; c0 < count; c0 += NB) {
-        tri_invit_batch<NB>(Zt, ldz, n, d, e, lam, pos, c0, count, tnorm, scr, piv);
+    int* ord = reinterpret_cast<int*>(pb);
+    int* list = ord + count;
+    bool redo = s_ok == 0;
+    if (!redo) {
+      tri_cluster_members(lam, pos, n, count, 1e-4f * tnorm, ord, list, &s_nl);
+      for (int c0 = 0; c0 < s_nl; c0 += NB) {
+        tri_invit_batch<NB>(Zt, ldz, n, d, e, lam, pos, list, c0, s_nl, tnorm, scr, piv, 1);
         __syncthreads();
       }
+      const int ldc = tri_ldz(count);
+      float* C = reinterpret_cast<float*>(scr_raw);
+      float* dinv = reinterpret_cast<float*>(scr_raw + tri_al16((size_t)(n / 2) * ((n / 2) | 1) * 4));
+      redo = !tri_cholqr<TRI_CU>(Zt, ldz, n, count, C, ldc, dinv, 0.25f);
     }
-    const int ldc = tri_ldz(count);
-    float* C = reinterpret_cast<float*>(scr_raw);
-    float* dinv = reinterpret_cast<float*>(scr_raw + tri_al16((size_t)(n / 2) * ((n / 2) | 1) * 4));
-    __syncthreads();
-    if (!tri_cholqr<TRI_CU>(Zt, ldz, n, count, C, ldc, dinv, 0.25f)) {
+    if (redo) {
       __syncthreads();
+      for (int c0 = 0; c0 < count; c0 += NB) {
+        tri_invit_batch<NB>(Zt, ldz, n, d, e, lam, pos, nullptr, c0, count, tnorm, scr, piv, 1);
+        __syncthreads();
+      }
       tri_cgs2(Zt, ldz, n, count, xb, red);
     }
   }

@@ -63,6 +63,7 @@ def load():
         "fd_create": [i64, i32, i32, dbl, i32, vp, ctypes.POINTER(vp)],
         "fd_append": [vp, vp, i64, i64, i32, i32],
         "fd_sketch": [vp, vp, i32, i32],
+        "fd_merge": [vp, vp],
         "fd_cov_err": [vp, vp, i64, i64, i32, i32, ctypes.POINTER(dbl)],
         "fd_cov_err_pair": [vp, i64, i64, i64, i32, vp, i64, i32, i32, vp,
                             ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
@@ -115,7 +116,8 @@ def _check(code: int, where: str):
 
 def _stream_ptr(stream):
     if stream is not None:
-        return ctypes.c_void_p(stream)
+        # a torch.cuda.Stream (or anything with a cuda_stream handle), or a raw handle
+        return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
     try:
         import torch
         if torch.cuda.is_available() and torch.cuda.is_initialized():
@@ -181,6 +183,10 @@ class FDSketch:
         _check(lib.fd_sketch(self._h, ctypes.c_void_p(B.ctypes.data), code, 0), "fd_sketch")
         return B
 
+    def merge(self, other: "FDSketch"):
+        """Fold ``other``'s stream into this sketch (fd_merge)."""
+        _check(load().fd_merge(self._h, other._h), "fd_merge")
+
     def cov_err(self, A) -> float:
         ptr, n, ld, code, dev, keep = _as_rows(A)
         out = ctypes.c_double()
@@ -231,6 +237,21 @@ class FDSketch:
             self.close()
         except Exception:
             pass
+
+
+def merge_tree(sketches):
+    """Merge a list of sketches pairwise, level by level ((0,1), (2,3), ...),
+    until one is left; returns it (the others keep their own state)."""
+    level = list(sketches)
+    while len(level) > 1:
+        nxt = []
+        for i in range(0, len(level) - 1, 2):
+            level[i].merge(level[i + 1])
+            nxt.append(level[i])
+        if len(level) % 2:
+            nxt.append(level[-1])
+        level = nxt
+    return level[0]
 
 
 def cov_err_noalloc(A, B, stream=None):

@@ -1,0 +1,113 @@
+"""fd_merge and merge trees vs the FP64 oracle replaying the same tree.
+
+A stream is cut into contiguous shards. Each shard is sketched by its own
+handle on its own CUDA stream, so the reductions of different shards run
+concurrently. The handles are then merged pairwise. The oracle replays the
+same shards and the same tree (``FDOracle.merge``). The parity bar is that of
+the single-stream tests: the sketch's singular values per the per-value
+allowance, cov-err within 1e-5, and the FP64 counters.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import cov_err, FDOracle
+from paper_1501_06561_gb300 import fd
+from paper_1501_06561_gb300 import workloads as W
+from helpers import COV_ABS, assert_sigma_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    fd.load()
+
+
+def _gpu_tree(A, cuts, ell, variant, alpha, prec):
+    streams = [torch.cuda.Stream() for _ in range(len(cuts) - 1)]
+    X = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    torch.cuda.synchronize()
+    sks = [fd.FDSketch(A.shape[1], ell, variant, alpha, prec, stream=st) for st in streams]
+    for s, a, b in zip(sks, cuts[:-1], cuts[1:]):
+        s.append(X[a:b])
+    root = fd.merge_tree(sks)
+    B = root.sketch()
+    st = root.stats()
+    for s in sks:
+        s.close()
+    return B, st
+
+
+def _oracle_tree(A, cuts, ell, variant, alpha):
+    os_ = []
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        o = FDOracle(A.shape[1], ell, variant, alpha)
+        o.append(A[a:b])
+        os_.append(o)
+    level = os_
+    while len(level) > 1:
+        nxt = []
+        for i in range(0, len(level) - 1, 2):
+            level[i].merge(level[i + 1])
+            nxt.append(level[i])
+        if len(level) % 2:
+            nxt.append(level[-1])
+        level = nxt
+    return level[0].sketch()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("variant,alpha", [("fd", 1.0), ("pfd", 0.4), ("isvd", 1.0)])
+def test_merge_tree_matches_oracle(variant, alpha, prec):
+    """4 shards of a 4,001 x 290 stream (ragged cut), ell = 21."""
+    A = W.random_noisy(4001, 290, m=10, seed=71, dtype=np.float32)
+    cuts = [0, 1100, 2000, 3333, 4001]
+    B, st = _gpu_tree(A, cuts, 21, variant, alpha, prec)
+    Bo, io = _oracle_tree(A, cuts, 21, variant, alpha)
+    assert abs(st["norm_a2"] - io["normA2"]) <= 1e-12 * io["normA2"]
+    assert st["n_seen"] == A.shape[0]
+    assert_sigma_parity(B, Bo, io["normA2"], prec, what=f"merge {variant}/{prec}")
+    ce_g, ce_o = cov_err(A, B), cov_err(A, Bo)
+    assert abs(ce_g - ce_o) <= COV_ABS, (ce_g, ce_o)
+    assert abs(st["sketch_sum_delta"] - io["sum_delta"]) <= 1e-4 * io["sum_delta"]
+    # the bound of Lemma 1 carried through the merges
+    if variant != "isvd":
+        assert ce_g * io["normA2"] <= st["sketch_sum_delta"] * (1 + 1e-3)
+
+
+def test_merge_tree_ss_short_streams():
+    """SS on short shards (one reduction each, P13), mass conserved."""
+    A = W.random_noisy(260, 64, m=6, seed=72, dtype=np.float32)
+    cuts = [0, 64, 130, 200, 260]
+    B, st = _gpu_tree(A, cuts, 20, "ss", 1.0, "fp32")
+    Bo, io = _oracle_tree(A, cuts, 20, "ss", 1.0)
+    assert_sigma_parity(B, Bo, io["normA2"], "fp32", what="merge ss")
+    assert abs(cov_err(A, B) - cov_err(A, Bo)) <= COV_ABS
+    na2 = float(np.sum(A.astype(np.float64) ** 2))
+    assert abs(float(np.sum(B * B)) - na2) <= 1e-5 * na2
+
+
+def test_merge_rejects_bad_pairs():
+    with fd.FDSketch(32, 4) as a, fd.FDSketch(33, 4) as b:
+        with pytest.raises(fd.FDError):
+            a.merge(b)
+        with pytest.raises(fd.FDError):
+            a.merge(a)
+
+
+def test_merge_of_fresh_sketch_changes_nothing():
+    A = W.random_noisy(900, 80, m=5, seed=73, dtype=np.float32)
+    with fd.FDSketch(80, 9) as a, fd.FDSketch(80, 9) as e:
+        a.append(torch.from_numpy(A).cuda())
+        B0 = a.sketch()
+        s0 = a.stats()
+        a.merge(e)
+        B1 = a.sketch()
+        s1 = a.stats()
+    np.testing.assert_array_equal(B0, B1)
+    assert s1["norm_a2"] == s0["norm_a2"] and s1["n_seen"] == s0["n_seen"]

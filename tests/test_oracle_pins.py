@@ -293,3 +293,70 @@ def test_isvd_fails_on_paper_adversarial():
     A = W.paper_adversarial(n=3000, d=120, m1=60, m2=4)
     e = {v: cov_err(A, fd_sketch(A, 20, v)[0]) for v in ("fd", "isvd")}
     assert e["fd"] < 0.5 * e["isvd"], e
+
+
+# ---- merge of two sketches -------------------------------------------------
+
+def _merged(A1, A2, ell, variant="fd", alpha=1.0):
+    o1 = FDOracle(A1.shape[1], ell, variant, alpha)
+    o2 = FDOracle(A2.shape[1], ell, variant, alpha)
+    o1.append(A1)
+    o2.append(A2)
+    o1.merge(o2)
+    return o1
+
+
+@pytest.mark.parametrize("variant", ["fd", "pfd", "isvd"])
+def test_merge_keeps_lemma1_bounds(variant):
+    """After a merge, 0 <= x^T (A^T A - B^T B) x <= sum of all deltas for the
+    union of both streams (Lemma 1, Sec. 3.1, applied to every reduction of
+    both streams), and the counters cover both streams."""
+    A1 = W.random_noisy(700, 40, m=6, seed=31)
+    A2 = W.random_noisy(450, 40, m=6, seed=32)
+    o = _merged(A1, A2, 8, variant, 0.5)
+    B, info = o.sketch()
+    A = np.vstack([A1, A2]).astype(np.float64)
+    lam = cov_spectrum(A, B)
+    na2 = float(np.sum(A * A))
+    assert abs(info["normA2"] - na2) <= 1e-12 * na2
+    assert info["n_seen"] == A.shape[0]
+    assert lam[0] >= -1e-10 * na2
+    assert lam[-1] <= info["sum_delta"] * (1 + 1e-10) + 1e-10 * na2
+    # a merge is not the same as one stream: at least the bound must not be free
+    assert info["sum_delta"] > 0.0
+
+
+def test_merge_exact_when_rank_fits():
+    """Rows spanning at most ell-1 dimensions in total: every delta is zero,
+    so the merged sketch reproduces A^T A exactly (Sec. 2.3, sigma_ell = 0)."""
+    basis = W.low_rank_rows(5, 30, 5, seed=7)
+    rng = np.random.default_rng(3)
+    A1 = rng.standard_normal((300, 5)) @ basis
+    A2 = rng.standard_normal((200, 5)) @ basis
+    o = _merged(A1, A2, 8)
+    B, info = o.sketch()
+    A = np.vstack([A1, A2])
+    assert cov_err(A, B) <= 1e-11
+    assert info["sum_delta"] <= 1e-9 * info["normA2"]
+
+
+def test_merge_ss_conserves_mass():
+    """SS keeps ||B||_F^2 = ||A||_F^2 (Sec. 3.1) through a merge as well."""
+    A1 = W.random_noisy(500, 30, m=5, seed=41)
+    A2 = W.random_noisy(333, 30, m=5, seed=42)
+    o = _merged(A1, A2, 6, "ss")
+    B, info = o.sketch()
+    A = np.vstack([A1, A2]).astype(np.float64)
+    na2 = float(np.sum(A * A))
+    assert abs(float(np.sum(B * B)) - na2) <= 1e-10 * na2
+
+
+def test_merge_of_empty_sketch_is_identity():
+    A1 = W.random_noisy(400, 20, m=4, seed=51)
+    o1 = FDOracle(20, 6, "fd")
+    o1.append(A1)
+    B0, i0 = o1.sketch()
+    o1.merge(FDOracle(20, 6, "fd"))
+    B1, i1 = o1.sketch()
+    np.testing.assert_array_equal(B0, B1)
+    assert i1["normA2"] == i0["normA2"] and i1["sum_delta"] == i0["sum_delta"]
