@@ -58,6 +58,7 @@ __device__ __forceinline__ double load_as_f64(const void* p, long long idx, int 
 // Shared memory map (bytes): region A 64 KB (Jacobi matrix / rotate staging),
 // region B 32 KB (Gram staging / rotate matrix), scalars.
 constexpr int TRI_NB = 16;        // inverse-iteration vectors per batch
+static_assert(BT / 32 * 32 * TRI_CPT >= BMAX_L, "step 1 of the solve covers 2*ell - 1 columns");
 constexpr size_t REG_A = ((size_t)BMAX_L * (BMAX_L | 1) * 4 + 15) / 16 * 16;
 constexpr size_t REG_B = (size_t)BMAX_L * RCH * 4;
 constexpr size_t SCAL = (size_t)BMAX_L * (4 * sizeof(double) + 2 * sizeof(int)) + BMAX_L * 4 + 256;
@@ -178,8 +179,9 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
     a.ldr = np;
     a.max_sweeps = max_sweeps;
     a.row_mass = s_mass;
-    tri_eig_shrink<TRI_NB, 4, 32, 1, 4>(a, A, ld, nrows, smax > 0.f ? (double)smax : 1.0, smem + REG_A,
-                                        smem + REG_A + tri_scratch_bytes(nrows, TRI_NB));
+    // step 1 of the solve works in the scratch area (272 n >= tri_rw_bytes(n, 8) bytes)
+    tri_eig_shrink<TRI_NB, 4, 32, 1>(a, A, ld, nrows, smax > 0.f ? (double)smax : 1.0, smem + REG_A,
+                                     smem + REG_A + tri_scratch_bytes(nrows, TRI_NB), smem + REG_A);
   } else {
   float* nrm = reinterpret_cast<float*>(sc);
   double* lam = reinterpret_cast<double*>(sc + BMAX_L * 4);

@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(NT) eig_fast_kernel(EigArgs a) {
 
 // Full-buffer FP32 reductions: Householder tridiagonalisation, bisection and
 // inverse iteration (fd_tridiag.cuh), G scaled by its largest diagonal entry.
-template <int NB, int R, int MAXJ, int VPT, int MAXT, bool GLOBAL>
+template <int NB, int R, int MAXJ, int VPT, bool GLOBAL>
 __global__ void __launch_bounds__(512, 1) eig_tri_kernel(EigArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = a.n;
@@ -326,6 +326,9 @@ __global__ void __launch_bounds__(512, 1) eig_tri_kernel(EigArgs a) {
   unsigned char* scr = GLOBAL ? reinterpret_cast<unsigned char*>(a.work) + tri_al16((size_t)n * ld * 4)
                               : smem_raw + tri_al16((size_t)n * ld * 4);
   unsigned char* small = GLOBAL ? smem_raw : scr + tri_scratch_bytes(n, NB);
+  // step-1 workspace: the scratch area while that is in shared memory
+  // (tri_config checks that it is large enough), else after `small`
+  unsigned char* rw = GLOBAL ? smem_raw + tri_small_bytes(n) : scr;
   __shared__ float s_max;
   eig_load<float>(a, A, ld, n, n);
   if (tid == 0) s_max = 0.f;
@@ -339,19 +342,19 @@ __global__ void __launch_bounds__(512, 1) eig_tri_kernel(EigArgs a) {
   const float inv = (smax > 0.f) ? 1.f / smax : 1.f;
   for (int idx = tid; idx < n * ld; idx += blockDim.x) A[idx] *= inv;
   __syncthreads();
-  tri_eig_shrink<NB, R, MAXJ, VPT, MAXT>(a, A, ld, n, (smax > 0.f) ? (double)smax : 1.0, scr, small);
+  tri_eig_shrink<NB, R, MAXJ, VPT>(a, A, ld, n, (smax > 0.f) ? (double)smax : 1.0, scr, small, rw);
 }
 
-template <int NB, int R, int MAXJ, int VPT, int MAXT, bool GLOBAL>
+template <int NB, int R, int MAXJ, int VPT, bool GLOBAL>
 cudaError_t launch_tri(const EigArgs& a, size_t smem, cudaStream_t st) {
   static size_t attr_set = 0;
   if (smem > attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(eig_tri_kernel<NB, R, MAXJ, VPT, MAXT, GLOBAL>,
+    cudaError_t e = cudaFuncSetAttribute(eig_tri_kernel<NB, R, MAXJ, VPT, GLOBAL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = smem;
   }
-  eig_tri_kernel<NB, R, MAXJ, VPT, MAXT, GLOBAL><<<1, 512, smem, st>>>(a);
+  eig_tri_kernel<NB, R, MAXJ, VPT, GLOBAL><<<1, 512, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -362,9 +365,10 @@ cudaError_t launch_tri(const EigArgs& a, size_t smem, cudaStream_t st) {
 // area in a global workspace of tri_global_bytes(n, 16) bytes.
 int tri_config(int n, int ell) {
   if (n != 2 * ell || n < 4) return 0;
-  if (n <= 128 && tri_smem_bytes(n, 32) <= 226 * 1024) return 1;
-  if (n <= 208 && tri_smem_bytes(n, 16) <= 226 * 1024) return 2;
-  if (n <= 208 && tri_smem_bytes(n, 8) <= 226 * 1024) return 3;
+  const size_t rw = tri_rw_bytes(n, 16);  // 512 threads
+  if (n <= 128 && tri_smem_bytes(n, 32) <= 226 * 1024 && tri_scratch_bytes(n, 32) >= rw) return 1;
+  if (n <= 208 && tri_smem_bytes(n, 16) <= 226 * 1024 && tri_scratch_bytes(n, 16) >= rw) return 2;
+  if (n <= 208 && tri_smem_bytes(n, 8) <= 226 * 1024 && tri_scratch_bytes(n, 8) >= rw) return 3;
   if (n <= 512) return 4;
   return 0;
 }
@@ -401,11 +405,11 @@ cudaError_t launch_eig_shrink(const EigArgs& a, cudaStream_t st) {
   const int np = a.n + (a.n & 1);
   if (sizeof(T) == 4 && a.use_tri) {
     const int cfg = tri_config(a.n, a.ell);
-    if (cfg == 1) return launch_tri<32, 8, 16, 1, 4, false>(a, tri_smem_bytes(a.n, 32), st);
-    if (cfg == 2) return launch_tri<16, 8, 26, 2, 7, false>(a, tri_smem_bytes(a.n, 16), st);
-    if (cfg == 3) return launch_tri<8, 8, 26, 2, 7, false>(a, tri_smem_bytes(a.n, 8), st);
+    if (cfg == 1) return launch_tri<32, 8, 16, 1, false>(a, tri_smem_bytes(a.n, 32), st);
+    if (cfg == 2) return launch_tri<16, 8, 26, 2, false>(a, tri_smem_bytes(a.n, 16), st);
+    if (cfg == 3) return launch_tri<8, 8, 26, 2, false>(a, tri_smem_bytes(a.n, 8), st);
     if (cfg == 4 && a.work != nullptr && a.work_bytes >= tri_global_bytes(a.n, 16))
-      return launch_tri<16, 16, 32, 2, 16, true>(a, tri_small_bytes(a.n), st);
+      return launch_tri<16, 16, 32, 2, true>(a, tri_small_bytes(a.n) + tri_rw_bytes(a.n, 16), st);
   }
   if (sizeof(T) == 4 && a.work == nullptr && np <= 224 && eig_fast_smem(np) <= 226 * 1024) {
     const size_t smem = eig_fast_smem(np);

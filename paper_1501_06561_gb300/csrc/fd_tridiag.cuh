@@ -39,7 +39,7 @@
 
 namespace fdk {
 
-constexpr int TRI_KR = 16;  // row slots per warp and batch in step 1
+constexpr int TRI_CPT = 4;  // trailing-block columns per thread in step 1
 
 __host__ __device__ constexpr size_t tri_al16(size_t b) { return (b + 15) / 16 * 16; }
 // offset (floats) of reflector s (length n-1-s) in the packed store
@@ -76,18 +76,25 @@ __host__ __device__ constexpr size_t tri_rest_bytes(int n, int NB) {
 __host__ __device__ constexpr size_t tri_global_bytes(int n, int NB) {
   return tri_al16((size_t)n * (size_t)(n | 1) * 4) + tri_scratch_bytes(n, NB);
 }
+// Step-1 workspace in shared memory: two packed (v, q, x) arrays of n float4
+// and the row groups' partial products (at most nw * min(n, 32 TRI_CPT)
+// floats). It is dead once step 1 ends, so it may share the scratch area.
+__host__ __device__ constexpr size_t tri_rw_bytes(int n, int nw) {
+  return 2 * tri_al16((size_t)n * 16) +
+         tri_al16((size_t)nw * (size_t)(n < 32 * TRI_CPT ? n : 32 * TRI_CPT) * 4);
+}
 // Shared-memory bytes of the whole solve for n rows (A with stride n | 1).
 __host__ __device__ constexpr size_t tri_smem_bytes(int n, int NB) {
   return tri_al16((size_t)n * (size_t)(n | 1) * 4) + tri_rest_bytes(n, NB);
 }
 
 // ---------------------------------------------------------------------------
-// Step 1. d (n) and e (n-1) receive T; xb, vb0, vb1, qb, pb: n floats each;
-// red: 64 floats.
+// Step 1. d (n) and e (n-1) receive T; red: 64 floats (16-byte aligned);
+// rw: tri_rw_bytes(n, warps) bytes of shared memory (16-byte aligned).
 // ---------------------------------------------------------------------------
-// Sum of the first nw (<= 32, a multiple of 4 or less than 4... any) floats
-// of a 16-byte aligned shared array: four-wide loads and a tree, so the
-// result waits on one load latency instead of nw dependent ones.
+// Sum of the first nw (<= 32) floats of a 16-byte aligned shared array:
+// four-wide loads and a tree, so the result waits on one load latency
+// instead of nw dependent ones.
 __device__ __forceinline__ float tri_sum_parts(const float* p, int nw) {
   float s[8];
 #pragma unroll
@@ -103,11 +110,111 @@ __device__ __forceinline__ float tri_sum_parts(const float* p, int nw) {
   return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 }
 
-template <int MAXT>  // column chunks of 32 per row: n - 1 <= 32 MAXT
-__device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, float* xb, float* vb0,
-                           float* vb1, float* qb, float* pb, float* red) {
+// One pass over the trailing block T (m x m, row stride ld) by the warps of
+// row group g (rows g, g + G, ...): apply the previous step's update
+// a_rc -= v_r q_c + q_r v_c and accumulate the column sums sum_r a_rc xh_r
+// of the updated block for U columns per thread (c0 + cs u). Pc[r] holds
+// (v_r, q_r, x_r) of the previous reflector and the current column; row 0
+// weighs xh0 instead of x_0. The symmetric block gives p = A v from column
+// sums, so no lane-to-lane reduction is needed. Writes the group's partial
+// p_c to pp[g m + c] and returns this thread's share of v^T p.
+template <int U>
+__device__ __forceinline__ float tri_pass(float* T, int ld, int m, const float4* Pc, float* pp,
+                                          int g, int G, int c0, int cs, float xh0, float scale) {
+  float vc[U], qc[U], wc[U], acc[U];
+  int col[U];
+  bool live[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int c = c0 + cs * u;
+    live[u] = c < m;
+    col[u] = live[u] ? c : m - 1;
+    const float4 pc = Pc[col[u]];
+    vc[u] = live[u] ? pc.x : 0.f;
+    qc[u] = live[u] ? pc.y : 0.f;
+    wc[u] = (c == 0) ? xh0 : pc.z;
+    acc[u] = 0.f;
+  }
+  int r = g;
+  if (g == 0) {  // row 0 weighs x_0 - alpha
+    const float4 pr = Pc[0];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      float a = T[col[u]];
+      a = fmaf(-pr.x, qc[u], fmaf(-pr.y, vc[u], a));
+      if (live[u]) T[col[u]] = a;
+      acc[u] = fmaf(a, xh0, acc[u]);
+    }
+    r = G;
+  }
+  for (; r + G < m; r += 2 * G) {  // two rows at a time: all loads first
+    const float4 p0 = Pc[r], p1 = Pc[r + G];
+    float* row0 = T + (size_t)r * ld;
+    float* row1 = row0 + (size_t)G * ld;
+    float a0[U], a1[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      a0[u] = row0[col[u]];
+      a1[u] = row1[col[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      a0[u] = fmaf(-p0.x, qc[u], fmaf(-p0.y, vc[u], a0[u]));
+      a1[u] = fmaf(-p1.x, qc[u], fmaf(-p1.y, vc[u], a1[u]));
+      if (live[u]) {
+        row0[col[u]] = a0[u];
+        row1[col[u]] = a1[u];
+      }
+      acc[u] = fmaf(a1[u], p1.z, fmaf(a0[u], p0.z, acc[u]));
+    }
+  }
+  if (r < m) {
+    const float4 pr = Pc[r];
+    float* row = T + (size_t)r * ld;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      float a = row[col[u]];
+      a = fmaf(-pr.x, qc[u], fmaf(-pr.y, vc[u], a));
+      if (live[u]) row[col[u]] = a;
+      acc[u] = fmaf(a, pr.z, acc[u]);
+    }
+  }
+  float kp = 0.f;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (live[u]) {
+      const float p = acc[u] * scale;
+      pp[g * m + col[u]] = p;
+      kp = fmaf(wc[u] * scale, p, kp);
+    }
+  }
+  return kp;
+}
+
+// sum_g pp[g m + i] over the G (<= 16) row groups: independent loads, tree sum
+__device__ __forceinline__ float tri_group_sum(const float* pp, int m, int i, int G) {
+  float t[16];
+#pragma unroll
+  for (int g = 0; g < 16; ++g) t[g] = (g < G) ? pp[g * m + i] : 0.f;
+#pragma unroll
+  for (int h = 8; h > 0; h >>= 1)
+#pragma unroll
+    for (int g = 0; g < h; ++g) t[g] += t[g + h];
+  return t[0];
+}
+
+// a / b for b in 1..4 without a division instruction
+__device__ __forceinline__ int tri_div14(int a, int b) {
+  return (b == 1) ? a : (b == 2) ? (a >> 1) : (b == 4) ? (a >> 2) : a / 3;
+}
+
+static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, unsigned char* rw,
+                                  float* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  float4* P0 = reinterpret_cast<float4*>(rw);
+  float4* P1 = reinterpret_cast<float4*>(rw + tri_al16((size_t)n * 16));
+  float* pp = reinterpret_cast<float*>(rw + 2 * tri_al16((size_t)n * 16));
   float* kpart = red;       // per-warp parts of K = v^T p
   float* npart = red + 32;  // per-warp parts of ||x||^2
   if (tid == 0) d[0] = A[0];
@@ -115,7 +222,7 @@ __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, float* x
     float sq = 0.f;
     for (int i = tid; i < n - 1; i += nt) {
       const float x = A[(size_t)(i + 1) * ld];
-      xb[i] = x;
+      P0[i] = make_float4(0.f, 0.f, x, 0.f);  // no previous step to apply
       sq = fmaf(x, x, sq);
     }
     sq = warp_sum(sq);
@@ -124,123 +231,65 @@ __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, float* x
   __syncthreads();
   for (int s = 0; s + 1 < n; ++s) {
     const int m = n - 1 - s;  // length of x_s = size of the trailing block
-    float* vcur = (s & 1) ? vb1 : vb0;
-    const float* vprv = (s & 1) ? vb0 : vb1;
+    const float4* Pc = (s & 1) ? P1 : P0;
+    float4* Pn = (s & 1) ? P0 : P1;
     // reflector s: v = (x - alpha e_1) / ||x - alpha e_1||, alpha = -sign(x_0) ||x||
     const float ss = tri_sum_parts(npart, nw);
-    const float x0 = xb[0];
+    const float x0 = Pc[0].z;
     float alpha = x0, scale = 0.f;  // a length-1 (or zero) column needs no reflection
     if (m > 1 && ss > 0.f) {
       const float nx = sqrtf(ss);
       alpha = (x0 >= 0.f) ? -nx : nx;
       scale = 1.f / sqrtf(2.f * (ss - x0 * alpha));
     }
+    const float xh0 = x0 - alpha;
     if (tid == 0) e[s] = alpha;
     if (m > 1) {
       float* vpk = A + tri_voff(n, s);  // inside rows 0..s, which are finished
-      for (int i = tid; i < m; i += nt) {
-        const float v = ((i == 0) ? (x0 - alpha) : xb[i]) * scale;
-        vcur[i] = v;
-        vpk[i] = v;
-      }
+      for (int i = tid; i < m; i += nt) vpk[i] = ((i == 0) ? xh0 : Pc[i].z) * scale;
     }
-    // trailing block rows/cols s+1..n-1: apply step s-1 (vprv, qb at offset
-    // +1) and accumulate p_s = A v_s. Warp w takes rows r = w + k nw
-    // (k < TRI_KR) with its lanes along each row; the row sums of all lanes
-    // are combined at the end by one butterfly over the TRI_KR row slots.
+    // trailing block rows/cols s+1..n-1: CW warps cover its columns (TRI_CPT
+    // per thread), G groups of CW warps split its rows
+    static_assert(TRI_CPT == 4, "the group arithmetic assumes 1 <= CW <= 4");
+    const int CW = (m + 32 * TRI_CPT - 1) / (32 * TRI_CPT);
+    const int G = tri_div14(nw, CW);
     {
-      const bool upd = s > 0;
-      const int tmax = (m + 31) >> 5;
-      float wc[MAXT], vc[MAXT], qc[MAXT];
-#pragma unroll
-      for (int t = 0; t < MAXT; ++t) {
-        const int c = lane + 32 * t;
-        wc[t] = vc[t] = qc[t] = 0.f;
-        if (c < m) {
-          wc[t] = ((c == 0) ? (x0 - alpha) : xb[c]) * scale;
-          if (upd) {
-            vc[t] = vprv[c + 1];
-            qc[t] = qb[c + 1];
-          }
-        }
-      }
+      const int g = tri_div14(warp, CW), cb = warp - g * CW;
       float kp = 0.f;
-      // rows r = warp + k nw in batches of TRI_KR slots (one batch unless a
-      // warp owns more than TRI_KR rows)
-      for (int kb = 0; warp + kb * nw < m; kb += TRI_KR) {
-        float acc[TRI_KR];
+      if (g < G) {
+        const int cs = 32 * CW, c0 = 32 * cb + lane;
+        int nu = 0;  // live column chunks of this warp: warp-uniform, >= 1
 #pragma unroll
-        for (int k = 0; k < TRI_KR; ++k) acc[k] = 0.f;
-#pragma unroll
-        for (int k0 = 0; k0 < TRI_KR; k0 += 4) {
-          if (warp + (kb + k0) * nw < m) {  // uniform across the warp
-#pragma unroll
-            for (int k = k0; k < k0 + 4; ++k) {
-              const int r = warp + (kb + k) * nw;
-              const bool rv = r < m;
-              const int rr = rv ? r : m - 1;
-              float* row = A + (size_t)(s + 1 + rr) * ld + (s + 1);
-              const float vr = (upd && rv) ? vprv[rr + 1] : 0.f;
-              const float qr = (upd && rv) ? qb[rr + 1] : 0.f;
-#pragma unroll
-              for (int t = 0; t < MAXT; ++t) {
-                if (t < tmax) {
-                  const int c = lane + 32 * t;
-                  if (c < m) {
-                    float a = row[c];
-                    if (upd) {
-                      a = fmaf(-vr, qc[t], fmaf(-qr, vc[t], a));
-                      if (rv) row[c] = a;
-                    }
-                    acc[k] = fmaf(a, wc[t], acc[k]);
-                  }
-                }
-              }
-            }
-          }
-        }
-        // butterfly over the 16 slots: lane l ends with slot (l >> 1) summed over all lanes
-        const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-        float l1[8], l2[4], l3[2];
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          l1[q] = (b4 ? acc[8 + q] : acc[q]) + __shfl_xor_sync(0xffffffffu, b4 ? acc[q] : acc[8 + q], 16);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          l2[q] = (b3 ? l1[4 + q] : l1[q]) + __shfl_xor_sync(0xffffffffu, b3 ? l1[q] : l1[4 + q], 8);
-#pragma unroll
-        for (int q = 0; q < 2; ++q)
-          l3[q] = (b2 ? l2[2 + q] : l2[q]) + __shfl_xor_sync(0xffffffffu, b2 ? l2[q] : l2[2 + q], 4);
-        float tot = (b1 ? l3[1] : l3[0]) + __shfl_xor_sync(0xffffffffu, b1 ? l3[0] : l3[1], 2);
-        tot += __shfl_xor_sync(0xffffffffu, tot, 1);
-        const int r = warp + (kb + (lane >> 1)) * nw;
-        if (!(lane & 1) && r < m) {
-          pb[r] = tot;
-          kp = fmaf(((r == 0) ? (x0 - alpha) : xb[r]) * scale, tot, kp);
-        }
+        for (int u = 0; u < TRI_CPT; ++u) nu += (32 * cb + cs * u < m);
+        float* T = A + (size_t)(s + 1) * ld + (s + 1);
+        if (nu == 4)      kp = tri_pass<4>(T, ld, m, Pc, pp, g, G, c0, cs, xh0, scale);
+        else if (nu == 3) kp = tri_pass<3>(T, ld, m, Pc, pp, g, G, c0, cs, xh0, scale);
+        else if (nu == 2) kp = tri_pass<2>(T, ld, m, Pc, pp, g, G, c0, cs, xh0, scale);
+        else              kp = tri_pass<1>(T, ld, m, Pc, pp, g, G, c0, cs, xh0, scale);
       }
       kp = warp_sum(kp);
       if (lane == 0) kpart[warp] = kp;
     }
     __syncthreads();
     if (m == 1) break;
-    // q_s, and column s+1 updated by step s: its diagonal is d[s+1], the
-    // rest is x_{s+1}
+    // q_s = 2 (p - K v), and column s+1 updated by step s: its diagonal is
+    // d[s+1], the rest is x_{s+1}; (v_s, q_s, x_{s+1}) go to Pn shifted by one
     {
       const float K = tri_sum_parts(kpart, nw);
-      const float v0 = vcur[0];
-      const float q0 = 2.f * fmaf(-K, v0, pb[0]);
+      const float v0 = xh0 * scale;
+      const float p0 = tri_group_sum(pp, m, 0, G);
+      const float q0 = 2.f * fmaf(-K, v0, p0);
       float sq = 0.f;
       for (int i = tid; i < m; i += nt) {
-        const float vi = vcur[i];
-        const float qi = 2.f * fmaf(-K, vi, pb[i]);
-        qb[i] = qi;
+        const float pi = tri_group_sum(pp, m, i, G);
+        const float vi = (i == 0) ? v0 : Pc[i].z * scale;
+        const float qi = 2.f * fmaf(-K, vi, pi);
         float a = A[(size_t)(s + 1 + i) * ld + (s + 1)];
         a = fmaf(-vi, q0, fmaf(-qi, v0, a));
         if (i == 0) {
           d[s + 1] = a;
         } else {
-          xb[i - 1] = a;
+          Pn[i - 1] = make_float4(vi, qi, a, 0.f);
           sq = fmaf(a, a, sq);
         }
       }
@@ -1110,13 +1159,15 @@ __device__ void tri_back_write(const EigArgs& a, const float* V, int n, const fl
 // The whole eigensolve + ReduceRank shrink + rotate-matrix write for a full
 // buffer of n = 2*ell rows whose Gram is in A (n x ld, scaled by 1/smax).
 // NB: vectors per fallback inverse-iteration batch; R, MAXJ, VPT: step-5
-// layout (n <= R * MAXJ); MAXT: step-1 column chunks (n - 1 <= 32 MAXT).
-// scr_raw: tri_scratch_bytes(n, NB) bytes; small: tri_small_bytes(n) bytes of
-// shared memory. A and scr_raw may be in shared or in global memory.
+// layout (n <= R * MAXJ). scr_raw: tri_scratch_bytes(n, NB) bytes; small:
+// tri_small_bytes(n) bytes of shared memory; rw: tri_rw_bytes(n, warps)
+// bytes of shared memory for step 1 (may be scr_raw when that is in shared
+// memory). A and scr_raw may be in shared or in global memory. Needs
+// n - 1 <= 32 TRI_CPT warps.
 // ---------------------------------------------------------------------------
-template <int NB, int R, int MAXJ, int VPT, int MAXT>
+template <int NB, int R, int MAXJ, int VPT>
 __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double smax,
-                               unsigned char* scr_raw, unsigned char* small) {
+                               unsigned char* scr_raw, unsigned char* small, unsigned char* rw) {
   constexpr int TRI_CU = (R * MAXJ / 2 + 31) / 32;  // retained vectors <= n / 2 <= 32 TRI_CU
   const int tid = threadIdx.x, nt = blockDim.x;
   double* mu = reinterpret_cast<double*>(small);
@@ -1140,7 +1191,7 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
   __shared__ int s_count, s_ok;
   __shared__ double s_dsum, s_dlast;
 
-  tri_reduce<MAXT>(A, ld, n, d, e, xb, vb0, vb1, qb, pb, red);
+  tri_reduce(A, ld, n, d, e, rw, red);
   tri_bisect(d, e, e2, n, lam, &s_tnorm, reinterpret_cast<int*>(scr_raw));
   {
     // eigenvalues at or below the bisection's resolution (2 eps lambda_1)
