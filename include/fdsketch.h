@@ -120,6 +120,20 @@ int fd_append(fd_handle h, const void* rows, int64_t n, int64_t ld, int32_t dtyp
  * output the call synchronises the stream. */
 int fd_sketch(fd_handle h, void* out, int32_t dtype, int32_t out_on_device);
 
+/* Compensative FD (Sec. 3.1, "Compensative Frequent Directions"): the sketch
+ * of fd_sketch, B = S' V^T, with every nonzero singular value replaced by
+ * sigma-hat_j = sqrt(sigma'_j^2 + Delta), Delta = sketch_sum_delta (every delta
+ * subtracted, the final flush included); V is unchanged and zero rows stay
+ * zero. The rows of a reduced sketch are orthogonal with norms sigma'_j, so
+ * each nonzero row is scaled by sqrt(1 + Delta / ||b_j||^2) (row norms in
+ * FP64); a sketch that never reduced has Delta = 0 and is returned as is.
+ * Same output contract as fd_sketch (ell x d, leading dimension d, FD_F32 or
+ * FD_F64, non-destructive; host output synchronises the stream).
+ * FD_EINVAL for variants other than FD_VAR_FD and FD_VAR_PFD, the ones whose
+ * sketch keeps 0 <= x^T (A^T A - B^T B) x <= Delta, which the compensated
+ * sketch turns into |x^T (A^T A - B-hat^T B-hat) x| <= Delta. */
+int fd_sketch_compensated(fd_handle h, void* out, int32_t dtype, int32_t out_on_device);
+
 /* Merge two sketches of the same width d. The paper states the problem for
  * streams that may be distributed (Sec. 1). src's current sketch (as
  * fd_sketch returns it, taken on a copy: src is unchanged) is appended to dst
@@ -142,6 +156,20 @@ int fd_merge(fd_handle dst, fd_handle src);
  * Synchronises the stream; *cov_err receives the value. */
 int fd_cov_err(fd_handle h, const void* A, int64_t n, int64_t ld, int32_t dtype,
                int32_t on_device, double* cov_err);
+
+/* proj-err (Sec. 1.1) of the current sketch B (as fd_sketch returns it) for
+ * the stream rows A (n x d, leading dimension ld, FD_F32 or FD_F64, on the
+ * device or on the host): ||A - pi_{B_k}(A)||_F^2 / ||A - A_k||_F^2, B_k the
+ * span of the top k right singular vectors of B (fewer if B has lower rank),
+ * A_k the best rank-k approximation of A. Numerator: ||A||_F^2 minus
+ * sum_j ||A v_j||^2, the v_j from an FP64 eigensolve of B B^T and one pass over
+ * A. Denominator: ||A||_F^2 minus the k largest eigenvalues of A^T A, found by
+ * Lanczos with full reorthogonalisation that streams A (never forms d x d) and
+ * stops when each carries a residual bound below 1e-10 ||A||_F^2. Returns 1.0
+ * when both are zero. 1 <= k < ell, else FD_EINVAL. Allocates its workspace
+ * and synchronises the handle's stream. */
+int fd_proj_err(fd_handle h, const void* A, int64_t n, int64_t ld, int32_t dtype,
+                int32_t on_device, int32_t k, double* proj_err);
 
 /* Same evaluator for a caller-given sketch B (rows x d, row-major FP32/FP64
  * per dtype, leading dimension d), without a handle. stream may be NULL. */

@@ -8,9 +8,11 @@ anything here, and this package never imports the product path.
 from .fd_oracle import (  # noqa: F401
     VARIANTS,
     FDOracle,
+    compensate,
     cov_err,
     cov_spectrum,
     fd_sketch,
+    proj_err,
     reduce_rank,
     shrink_index_split,
 )

@@ -36,6 +36,10 @@ What it follows
 * ``cov_err`` (Sec. 1.1): ``||A^T A - B^T B||_2 / ||A||_F^2`` with the
   spectral norm taken as the largest absolute eigenvalue of the explicit
   ``d x d`` difference (numpy ``eigvalsh``, a library primitive).
+* ``compensate`` (Compensative FD, Sec. 3.1): the final sketch ``S' V^T``
+  becomes ``S-hat V^T`` with ``sigma-hat_j = sqrt(sigma'_j^2 + Delta)``.
+* ``proj_err`` (Sec. 1.1): ``||A - pi_{B_k}(A)||_F^2 / ||A - A_k||_F^2`` with
+  ``B_k`` the top ``k`` right singular vectors of ``B``.
 
 Readings taken where the paper is silent or ambiguous (each is listed in
 the design notes): the buffer size and cadence, PFD and SS in a buffer of
@@ -279,6 +283,16 @@ class FDOracle:
         return B, info
 
 
+    def sketch_compensated(self):
+        """Compensative FD (Sec. 3.1): ``(compensate(B, Delta), info)`` for the
+        sketch ``B`` of ``sketch()`` and ``Delta = info["sum_delta"]`` (every
+        delta subtracted, the final flush included). FD and PFD only: their
+        sketches keep ``0 <= x^T (A^T A - B^T B) x <= Delta``."""
+        if self.variant not in ("fd", "pfd"):
+            raise ValueError("compensative FD is defined on FD and PFD sketches")
+        B, info = self.sketch()
+        return compensate(B, info["sum_delta"]), info
+
     def merge(self, other: "FDOracle"):
         """Fold ``other``'s stream into this sketch (merge of two sketches).
 
@@ -356,3 +370,51 @@ def cov_err(A, B, normA2: float | None = None) -> float:
     if normA2 == 0.0:
         return 0.0
     return float(max(abs(lam[0]), abs(lam[-1])) / normA2)
+
+
+def _rank_floor(sigma, shape) -> float:
+    """Numerical-rank floor of an FP64 SVD: largest value x size x eps."""
+    return sigma[0] * max(shape) * np.finfo(np.float64).eps if sigma.size else 0.0
+
+
+def compensate(B, sum_delta: float) -> np.ndarray:
+    """Compensative FD (Sec. 3.1): write ``B = S' V^T`` (SVD) and return
+    ``S-hat V^T`` with ``sigma-hat_j = sqrt(sigma'_j^2 + Delta)``.
+
+    Reading: only the nonzero singular values (above the FP64 rank floor) are
+    compensated. A zero singular value has no direction in ``B``, so the rows
+    past the rank stay zero. Rows come out by ``sigma'`` descending.
+    """
+    B = np.asarray(B, dtype=np.float64)
+    sigma, V = _svd_rows(B)
+    r = int(np.sum(sigma > _rank_floor(sigma, B.shape)))
+    out = np.zeros_like(B)
+    out[:r] = np.sqrt(sigma[:r] ** 2 + float(sum_delta))[:, None] * V[:r]
+    return out
+
+
+def proj_err(A, B, k: int = 10) -> float:
+    """proj-err (Sec. 1.1): ``||A - pi_{B_k}(A)||_F^2 / ||A - A_k||_F^2``.
+
+    ``B_k`` spans the top ``k`` right singular vectors of ``B`` (fewer when
+    ``B`` has rank below ``k``). The numerator sums, over row chunks of ``A``,
+    the squared residual of each row after projection onto ``B_k``; the
+    denominator is the sum of all but the ``k`` largest eigenvalues of
+    ``A^T A`` (numpy ``eigvalsh``), i.e. ``||A - A_k||_F^2``. Returns 1.0
+    when both are zero (``A`` of rank at most ``k``, captured exactly).
+    """
+    B = np.asarray(B, dtype=np.float64)
+    sigma, V = _svd_rows(B)
+    r = min(k, int(np.sum(sigma > _rank_floor(sigma, B.shape))))
+    Vk = V[:r]
+    A = np.asarray(A)
+    num = 0.0
+    for i in range(0, A.shape[0], 8192):
+        X = A[i:i + 8192].astype(np.float64)
+        R = X - (X @ Vk.T) @ Vk
+        num += float(np.sum(R * R))
+    lam = np.linalg.eigvalsh(_gram64(A))  # ascending
+    den = float(np.sum(lam[:max(lam.shape[0] - k, 0)]))
+    if den <= 0.0:
+        return 1.0 if num <= 0.0 else math.inf
+    return num / den

@@ -449,6 +449,22 @@ extern "C" int fd_sketch(fd_handle h, void* out, int32_t dtype, int32_t out_on_d
   return FD_OK;
 }
 
+// Compensative FD: the sketch, then each nonzero row rescaled (see fdsketch.h).
+extern "C" int fd_sketch_compensated(fd_handle h, void* out, int32_t dtype, int32_t out_on_device) {
+  if (!h || !out || (dtype != FD_F32 && dtype != FD_F64)) return FD_EINVAL;
+  if (h->variant != FD_VAR_FD && h->variant != FD_VAR_PFD) return FD_EINVAL;
+  const int dst_f64 = (dtype == FD_F64);
+  void* dev = out_on_device ? out : h->outdev;
+  int rc = fd_sketch(h, dev, dtype, 1);
+  if (rc != FD_OK) return rc;
+  FD_CK(launch_compensate_rows(dev, dst_f64, h->d, h->ell, h->d, h->ctr_flush, h->st));
+  if (out_on_device) return FD_OK;
+  FD_CK(cudaMemcpyAsync(out, h->outdev, (size_t)h->ell * h->d * (dst_f64 ? 8 : 4),
+                        cudaMemcpyDeviceToHost, h->st));
+  FD_CK(cudaStreamSynchronize(h->st));
+  return FD_OK;
+}
+
 // Merge: src's sketch rows become stream rows of dst (see fdsketch.h).
 extern "C" int fd_merge(fd_handle dst, fd_handle src) {
   if (!dst || !src || dst == src || dst->d != src->d) return FD_EINVAL;
@@ -586,6 +602,79 @@ extern "C" int fd_cov_err(fd_handle h, const void* A, int64_t n, int64_t ld, int
   cudaStreamSynchronize(h->st);
   cudaFree(B);
   if (tmp) cudaFree(tmp);
+  return rc;
+}
+
+// proj-err of the current sketch against the rows A (see fdsketch.h).
+extern "C" int fd_proj_err(fd_handle h, const void* A, int64_t n, int64_t ld, int32_t dtype,
+                           int32_t on_device, int32_t k, double* proj_err) {
+  if (!h || !A || !proj_err || ld < h->d || n < 1 || k < 1 || k >= h->ell) return FD_EINVAL;
+  if (dtype != FD_F32 && dtype != FD_F64) return FD_EINVAL;
+  const int ell = h->ell;
+  const int64_t d = h->d;
+  const int np = ell + (ell & 1);
+  const int slices = gram_simt_slices(d, 1);
+  double *B = nullptr, *parts = nullptr, *work = nullptr, *wrot = nullptr, *R = nullptr;
+  DevCounters* ctr = nullptr;
+  void* tmp = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(B); cudaFree(parts); cudaFree(work); cudaFree(wrot); cudaFree(R); cudaFree(ctr);
+    cudaFree(tmp);
+  };
+  const bool big = !eig_fits_smem(ell, 8);
+  if (cudaMalloc(&B, sizeof(double) * (size_t)ell * d) != cudaSuccess ||
+      cudaMalloc(&parts, sizeof(double) * (size_t)slices * np * np) != cudaSuccess ||
+      (big && cudaMalloc(&work, sizeof(double) * (size_t)np * np) != cudaSuccess) ||
+      cudaMalloc(&wrot, sizeof(double) * (size_t)k * ell) != cudaSuccess ||
+      cudaMalloc(&R, sizeof(double) * (size_t)k * d) != cudaSuccess ||
+      cudaMalloc(&ctr, 2 * sizeof(DevCounters)) != cudaSuccess) {
+    cleanup();
+    set_cuda_error(cudaErrorMemoryAllocation, "proj-err workspace");
+    return FD_ENOMEM;
+  }
+  // the sketch as fd_sketch returns it, in FP64 on the device
+  int rc = fd_sketch(h, B, FD_F64, 1);
+  if (rc != FD_OK) { cleanup(); return rc; }
+  // top k right singular vectors of B: an eigensolve of B B^T whose
+  // ReduceRank is the iSVD rule with ell' = k + 1 (the k largest values kept,
+  // the rest zeroed), then the rotate gives the rows sigma_j v_j
+  EigArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.parts = parts;
+  a.nparts = slices;
+  a.ldp = np;
+  a.part_stride = (long long)np * np;
+  a.symmetrize = 1;
+  a.n = ell;
+  a.ell = k + 1;
+  a.variant = FD_VAR_ISVD;
+  a.alpha = 1.0;
+  a.work = work;
+  a.ldw_work = np;
+  a.work_bytes = big ? sizeof(double) * (size_t)np * np : 0;
+  a.ctr_in = ctr;
+  a.ctr_out = ctr + 1;
+  a.wrot = wrot;
+  a.ldr = ell;
+  a.max_sweeps = 40;
+  a.tol = 4.0 * 1.1102230246251565e-16 * std::sqrt((double)np);
+  a.use_tri = 0;
+  FD_CK(cudaMemsetAsync(ctr, 0, 2 * sizeof(DevCounters), h->st));
+  FD_CK((launch_gram_simt<double>(B, d, ell, d, parts, np, 1, h->st)));
+  FD_CK(launch_eig_shrink<double>(a, h->st));
+  FD_CK((launch_rotate_simt<double>(wrot, ell, k, ell, B, d, R, d, d, h->st)));
+  const void* Ad = A;
+  if (!on_device) {
+    const size_t bytes = (size_t)n * ld * dtype_size(dtype);
+    cudaError_t e = cudaMalloc(&tmp, bytes);
+    if (e != cudaSuccess) { cleanup(); set_cuda_error(e, "cudaMalloc A"); return FD_ENOMEM; }
+    e = cudaMemcpyAsync(tmp, A, bytes, cudaMemcpyHostToDevice, h->st);
+    if (e != cudaSuccess) { cleanup(); set_cuda_error(e, "copy A"); return FD_ECUDA; }
+    Ad = tmp;
+  }
+  rc = proj_err_device(Ad, n, d, ld, dtype == FD_F64, R, k, h->st, proj_err, nullptr, nullptr);
+  cudaStreamSynchronize(h->st);
+  cleanup();
   return rc;
 }
 

@@ -7,6 +7,13 @@
 // bisection (extreme Ritz values) and inverse iteration (their residual
 // bounds beta_k |s_k|). Iteration stops once both extreme Ritz values carry a
 // residual bound below 1e-10 ||A||_F^2, or the Krylov space is exhausted.
+//
+// Projection-error evaluator: proj-err(A, B) = ||A - pi_{B_k}(A)||_F^2 /
+// ||A - A_k||_F^2 (Sec. 1.1). The same Lanczos on M = A^T A gives the k
+// largest eigenvalues (stopped once each carries a residual bound below
+// 1e-10 ||A||_F^2), so ||A - A_k||_F^2 = ||A||_F^2 - sum of them; one more
+// pass over A gives sum_j ||A v_j||^2 for the top right singular vectors v_j
+// of B, so the numerator is ||A||_F^2 minus that sum.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -268,9 +275,41 @@ __global__ void tri_check_kernel(const double* __restrict__ alpha, const double*
   out[3] = bk * smax;
 }
 
+// The topk largest Ritz values (descending) and their residual bounds
+// beta_k |s_k|: out[i] = theta_i, out[topk + i] = bound_i (zero past k).
+// One thread per value; scratch: 2 k doubles per thread.
+__global__ void tri_topk_kernel(const double* __restrict__ alpha, const double* __restrict__ beta,
+                                int k, int topk, double* __restrict__ scratch,
+                                double* __restrict__ out) {
+  const int i = threadIdx.x;
+  if (i >= topk) return;
+  if (i >= k) {
+    out[i] = 0.0;
+    out[topk + i] = 0.0;
+    return;
+  }
+  double lo = 1e300, hi = -1e300;
+  for (int q = 0; q < k; ++q) {
+    const double r = (q > 0 ? fabs(beta[q - 1]) : 0.0) + (q < k - 1 ? fabs(beta[q]) : 0.0);
+    lo = fmin(lo, alpha[q] - r);
+    hi = fmax(hi, alpha[q] + r);
+  }
+  const double span = fmax(hi - lo, 1e-300);
+  lo -= 1e-12 * span;
+  hi += 1e-12 * span;
+  const double th = tri_eig(alpha, beta, k, k - 1 - i, lo, hi);
+  const double sk = tri_last_component(alpha, beta, k, th, scratch + (size_t)2 * k * i,
+                                       scratch + (size_t)2 * k * i + k, 1e-14 * span);
+  out[i] = th;
+  out[topk + i] = fabs(beta[k - 1]) * sk;
+}
+
+// topk = 0: extreme eigenvalues of M (cov-err). topk > 0: the topk largest
+// eigenvalues into top_out (descending). norm_out (optional): ||A||_F^2.
 template <typename TA, typename TB>
 int run_lanczos(const TA* A, int64_t n, int64_t d, int64_t lda, const TB* B, int64_t rows,
-                int64_t ldb, cudaStream_t st, double* cov, double* lmin, double* lmax) {
+                int64_t ldb, cudaStream_t st, double* cov, double* lmin, double* lmax,
+                int topk = 0, double* top_out = nullptr, double* norm_out = nullptr) {
   const int kmax = (int)std::min<int64_t>(d, 1200);
   const int ct = (int)((d + 127) / 128);
   const int nchunks = std::max(1, std::min<int>((int)((n + 255) / 256), 608 / std::max(1, ct)));
@@ -296,8 +335,8 @@ int run_lanczos(const TA* A, int64_t n, int64_t d, int64_t lda, const TB* B, int
   CE_ALLOC(tb, std::max<int64_t>(rows, 1));
   CE_ALLOC(al, kmax + 1);
   CE_ALLOC(be, kmax + 1);
-  CE_ALLOC(sc, 2 * (kmax + 1));
-  CE_ALLOC(res, 4);
+  CE_ALLOC(sc, 2 * (size_t)(kmax + 1) * std::max(1, topk));
+  CE_ALLOC(res, std::max(4, 2 * topk));
   CE_ALLOC(na, 1);
 #undef CE_ALLOC
   const int rows_blocks = 608;
@@ -315,7 +354,7 @@ int run_lanczos(const TA* A, int64_t n, int64_t d, int64_t lda, const TB* B, int
   start_kernel<<<dblocks, CE_THREADS, 0, st>>>(w, d);
   dot_kernel<<<1, 1024, 0, st>>>(w, w, d, c);
   normalize_kernel<<<dblocks, CE_THREADS, 0, st>>>(w, c, V, c + 1, d);
-  std::vector<double> h(4);
+  std::vector<double> h(std::max(4, 2 * topk));
   double h_norm = 0.0;
   int k = 0;
   for (int j = 0; j < kmax; ++j) {
@@ -336,25 +375,153 @@ int run_lanczos(const TA* A, int64_t n, int64_t d, int64_t lda, const TB* B, int
     k = j + 1;
     const bool last = (k == kmax);
     if (k >= 4 && ((k % 8) == 0 || last)) {
-      tri_check_kernel<<<1, 32, 0, st>>>(al, be, k, sc, res);
-      cudaError_t e = cudaMemcpyAsync(h.data(), res, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
+      const int nres = topk > 0 ? 2 * topk : 4;
+      if (topk > 0)
+        tri_topk_kernel<<<1, ((topk + 31) / 32) * 32, 0, st>>>(al, be, k, topk, sc, res);
+      else
+        tri_check_kernel<<<1, 32, 0, st>>>(al, be, k, sc, res);
+      cudaError_t e = cudaMemcpyAsync(h.data(), res, nres * sizeof(double), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(&h_norm, na, sizeof(double), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) { set_cuda_error(e, "cov-err lanczos"); cleanup(); return FD_ECUDA; }
       const double tol = 1e-10 * std::max(h_norm, 1e-300);
-      if ((h[2] <= tol && h[3] <= tol) || last) break;
+      bool conv = true;
+      if (topk > 0) {
+        for (int i = 0; i < topk; ++i) conv = conv && (h[topk + i] <= tol);
+      } else {
+        conv = (h[2] <= tol && h[3] <= tol);
+      }
+      if (conv || last) break;
     }
   }
   cudaError_t e = cudaGetLastError();
   cleanup();
   if (e != cudaSuccess) { set_cuda_error(e, "cov-err kernels"); return FD_ECUDA; }
+  if (norm_out) *norm_out = h_norm;
+  if (topk > 0) {
+    for (int i = 0; i < topk; ++i) top_out[i] = h[i];
+    return FD_OK;
+  }
   *lmin = h[0];
   *lmax = h[1];
   *cov = (h_norm > 0.0) ? std::max(std::fabs(h[0]), std::fabs(h[1])) / h_norm : 0.0;
   return FD_OK;
 }
 
+// rinv2[j] = 1 / ||r_j||^2 (0 for a zero row), one warp per row of R (k x d).
+__global__ void row_inv_norm2_kernel(const double* __restrict__ R, int k, int64_t d,
+                                     double* __restrict__ rinv2) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j = w; j < k; j += blockDim.x >> 5) {
+    double acc = 0.0;
+    for (int64_t c = lane; c < d; c += 32) acc = fma(R[(int64_t)j * d + c], R[(int64_t)j * d + c], acc);
+    acc = warp_sum_t(acc);
+    if (lane == 0) rinv2[j] = (acc > 0.0) ? 1.0 / acc : 0.0;
+  }
+}
+
+template <typename TA>
+__global__ void cast_rows_kernel(const double* __restrict__ R, int64_t cnt, TA* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (TA)R[i];
+}
+
+// partial[block] = sum over the block's rows a_i of sum_j (a_i . r_j)^2 / ||r_j||^2:
+// one warp per row, eight vectors at a time, FP32 products in groups of 8
+// added into FP64 (as rows_dot_kernel).
+template <typename TA>
+__global__ void proj_rows_kernel(const TA* __restrict__ A, int64_t n, int64_t d, int64_t lda,
+                                 const TA* __restrict__ R, const double* __restrict__ rinv2,
+                                 int k, double* __restrict__ partial) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double mine = 0.0;
+  for (int64_t i = gw; i < n; i += nw) {
+    const TA* a = A + i * lda;
+    double rowsum = 0.0;
+    for (int j0 = 0; j0 < k; j0 += 8) {
+      double acc[8];
+      TA part[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) { acc[u] = 0.0; part[u] = TA(0); }
+      int cnt = 0;
+      for (int64_t c = lane; c < d; c += 32) {
+        const TA av = a[c];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (j0 + u < k) part[u] = fma(av, R[(int64_t)(j0 + u) * d + c], part[u]);
+        if (++cnt == 8) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) { acc[u] += (double)part[u]; part[u] = TA(0); }
+          cnt = 0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const double t = warp_sum_t(acc[u] + (double)part[u]);
+        if (j0 + u < k) rowsum += t * t * rinv2[j0 + u];
+      }
+    }
+    mine += rowsum;  // identical in every lane
+  }
+  __shared__ double red[32];
+  if (lane == 0) red[warp] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    partial[blockIdx.x] = s;
+  }
+}
+
+template <typename TA>
+int run_proj(const TA* A, int64_t n, int64_t d, int64_t lda, const double* R, int k,
+             cudaStream_t st, double* pe, double* num_out, double* den_out) {
+  std::vector<double> top(k);
+  double na2 = 0.0, dummy = 0.0;
+  int rc = run_lanczos<TA, double>(A, n, d, lda, nullptr, 0, d, st, &dummy, &dummy, &dummy, k,
+                                   top.data(), &na2);
+  if (rc != FD_OK) return rc;
+  const int blocks = 608;
+  double *rinv2 = nullptr, *part = nullptr, *out = nullptr;
+  TA* Rt = nullptr;
+  auto cleanup = [&]() { cudaFree(rinv2); cudaFree(part); cudaFree(out); cudaFree(Rt); };
+  if (cudaMalloc(&rinv2, sizeof(double) * k) != cudaSuccess ||
+      cudaMalloc(&part, sizeof(double) * blocks) != cudaSuccess ||
+      cudaMalloc(&out, sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&Rt, sizeof(TA) * (size_t)k * d) != cudaSuccess) {
+    cleanup();
+    set_cuda_error(cudaErrorMemoryAllocation, "proj-err workspace");
+    return FD_ENOMEM;
+  }
+  row_inv_norm2_kernel<<<1, 256, 0, st>>>(R, k, d, rinv2);
+  cast_rows_kernel<TA><<<256, 256, 0, st>>>(R, (int64_t)k * d, Rt);
+  proj_rows_kernel<TA><<<blocks, CE_THREADS, 0, st>>>(A, n, d, lda, Rt, rinv2, k, part);
+  sum_kernel<<<1, 1024, 0, st>>>(part, blocks, out);
+  double cap = 0.0;
+  cudaError_t e = cudaMemcpyAsync(&cap, out, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) { set_cuda_error(e, "proj-err kernels"); return FD_ECUDA; }
+  double topsum = 0.0;
+  for (int i = 0; i < k; ++i) topsum += top[i];
+  const double num = na2 - cap, den = na2 - topsum;
+  if (num_out) *num_out = num;
+  if (den_out) *den_out = den;
+  if (den <= 0.0) *pe = (num <= 0.0) ? 1.0 : INFINITY;
+  else *pe = num / den;
+  return FD_OK;
+}
+
 }  // namespace
+
+int proj_err_device(const void* A, int64_t n, int64_t d, int64_t lda, int a_f64, const double* R,
+                    int k, cudaStream_t st, double* pe, double* num, double* den) {
+  if (a_f64) return run_proj<double>((const double*)A, n, d, lda, R, k, st, pe, num, den);
+  return run_proj<float>((const float*)A, n, d, lda, R, k, st, pe, num, den);
+}
 
 int cov_err_device(const void* A, int64_t n, int64_t d, int64_t lda, int a_f64, const void* B,
                    int64_t rows, int64_t ldb, int b_f64, cudaStream_t st, double* cov,

@@ -85,6 +85,9 @@ cudaError_t launch_last_nonzero_row(const void* src, int src_f64, int64_t lds, i
 
 cudaError_t launch_merge_counters(DevCounters* dst, const DevCounters* src, cudaStream_t st);
 
+cudaError_t launch_compensate_rows(void* B, int b_f64, int64_t ld, int rows, int64_t d,
+                                   const DevCounters* ctr, cudaStream_t st);
+
 // --- tensor-core path (fd_tc.cu) ---------------------------------------------
 struct TcPlanes;  // opaque, defined in fd_tc.cu
 int tc_available();
@@ -93,6 +96,12 @@ int tc_available();
 int cov_err_device(const void* A, int64_t n, int64_t d, int64_t lda, int a_f64,
                    const void* B, int64_t rows, int64_t ldb, int b_f64,
                    cudaStream_t st, double* cov, double* lmin, double* lmax);
+
+// proj-err evaluator (fd_coverr.cu): R holds k rows sigma_j v_j (FP64, k x d,
+// zero rows allowed) spanning B_k; num and den (optional) receive the two
+// squared Frobenius norms.
+int proj_err_device(const void* A, int64_t n, int64_t d, int64_t lda, int a_f64, const double* R,
+                    int k, cudaStream_t st, double* pe, double* num, double* den);
 
 // Records the text of the last failing CUDA call (for fd_strerror).
 void set_cuda_error(cudaError_t e, const char* where);

@@ -557,6 +557,48 @@ cudaError_t launch_norm_b2(const void* src, int src_f64, int64_t lds, int rows, 
   return cudaGetLastError();
 }
 
+// Compensative FD (Sec. 3.1): row r of a sketch with orthogonal rows, norm
+// sigma'_r, is scaled by sqrt((sigma'_r^2 + Delta) / sigma'_r^2); zero rows stay
+// zero. One block per row, the squared norm in FP64.
+__global__ void compensate_rows_kernel(void* __restrict__ B, int b_f64, int64_t ld, int64_t d,
+                                       const DevCounters* __restrict__ ctr) {
+  const int64_t r = blockIdx.x;
+  __shared__ double red[32];
+  __shared__ double s_f;
+  double acc = 0.0;
+  for (int64_t k = threadIdx.x; k < d; k += blockDim.x) {
+    const double v = b_f64 ? reinterpret_cast<const double*>(B)[r * ld + k]
+                           : (double)reinterpret_cast<const float*>(B)[r * ld + k];
+    acc = fma(v, v, acc);
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    s_f = (s > 0.0) ? sqrt((s + ctr->sum_delta) / s) : 1.0;
+  }
+  __syncthreads();
+  const double f = s_f;
+  for (int64_t k = threadIdx.x; k < d; k += blockDim.x) {
+    if (b_f64) {
+      double* x = reinterpret_cast<double*>(B) + r * ld + k;
+      *x *= f;
+    } else {
+      float* x = reinterpret_cast<float*>(B) + r * ld + k;
+      *x = (float)((double)*x * f);
+    }
+  }
+}
+
+cudaError_t launch_compensate_rows(void* B, int b_f64, int64_t ld, int rows, int64_t d,
+                                   const DevCounters* ctr, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  compensate_rows_kernel<<<rows, 256, 0, st>>>(B, b_f64, ld, d, ctr);
+  return cudaGetLastError();
+}
+
 // Rows of a sketch up to its last nonzero one (1 + index, 0 if all zero):
 // one warp per row, block-wide maximum.
 __global__ void last_nonzero_row_kernel(const void* __restrict__ src, int src_f64, int64_t lds,

@@ -63,8 +63,10 @@ def load():
         "fd_create": [i64, i32, i32, dbl, i32, vp, ctypes.POINTER(vp)],
         "fd_append": [vp, vp, i64, i64, i32, i32],
         "fd_sketch": [vp, vp, i32, i32],
+        "fd_sketch_compensated": [vp, vp, i32, i32],
         "fd_merge": [vp, vp],
         "fd_cov_err": [vp, vp, i64, i64, i32, i32, ctypes.POINTER(dbl)],
+        "fd_proj_err": [vp, vp, i64, i64, i32, i32, i32, ctypes.POINTER(dbl)],
         "fd_cov_err_pair": [vp, i64, i64, i64, i32, vp, i64, i32, i32, vp,
                             ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
         "fd_stats": [vp, ctypes.POINTER(Stats)],
@@ -183,6 +185,21 @@ class FDSketch:
         _check(lib.fd_sketch(self._h, ctypes.c_void_p(B.ctypes.data), code, 0), "fd_sketch")
         return B
 
+    def sketch_compensated(self, out=None, dtype=np.float64):
+        """Compensative FD sketch (fd_sketch_compensated); FD and PFD only."""
+        lib = load()
+        if out is not None:
+            import torch
+            code = F64 if out.dtype == torch.float64 else F32
+            _check(lib.fd_sketch_compensated(self._h, ctypes.c_void_p(out.data_ptr()), code, 1),
+                   "fd_sketch_compensated")
+            return out
+        B = np.empty((self.ell, self.d), dtype=dtype)
+        code = F64 if B.dtype == np.float64 else F32
+        _check(lib.fd_sketch_compensated(self._h, ctypes.c_void_p(B.ctypes.data), code, 0),
+               "fd_sketch_compensated")
+        return B
+
     def merge(self, other: "FDSketch"):
         """Fold ``other``'s stream into this sketch (fd_merge)."""
         _check(load().fd_merge(self._h, other._h), "fd_merge")
@@ -191,6 +208,14 @@ class FDSketch:
         ptr, n, ld, code, dev, keep = _as_rows(A)
         out = ctypes.c_double()
         _check(load().fd_cov_err(self._h, ptr, n, ld, code, dev, ctypes.byref(out)), "fd_cov_err")
+        return out.value
+
+    def proj_err(self, A, k: int = 10) -> float:
+        """||A - pi_{B_k}(A)||_F^2 / ||A - A_k||_F^2 of the current sketch (fd_proj_err)."""
+        ptr, n, ld, code, dev, keep = _as_rows(A)
+        out = ctypes.c_double()
+        _check(load().fd_proj_err(self._h, ptr, n, ld, code, dev, int(k), ctypes.byref(out)),
+               "fd_proj_err")
         return out.value
 
     def stats(self) -> dict:

@@ -5,8 +5,9 @@ ReduceRank values (golden file), a replay of the whole stream in covariance
 form (eigendecomposition of the d x d matrix instead of the SVD of the rows),
 exact recovery of low-rank input, Properties 1-3 and Lemmas 1 and 3 (Sec. 3.1),
 the alpha-FD error bound (Theorem, Sec. 3.1), the SS mass identity and bound
-(Theorem on SpaceSaving Directions, Sec. 3.1), and closed forms / brute force
-for the covariance error (Sec. 1.1).
+(Theorem on SpaceSaving Directions, Sec. 3.1), closed forms / brute force
+for the covariance error and the projection error (Sec. 1.1), and the bounds
+of compensative FD (Sec. 3.1).
 """
 import json
 import math
@@ -15,7 +16,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle import FDOracle, cov_err, cov_spectrum, fd_sketch, reduce_rank
+from oracle import FDOracle, compensate, cov_err, cov_spectrum, fd_sketch, proj_err, reduce_rank
 from paper_1501_06561_gb300 import workloads as W
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -360,3 +361,79 @@ def test_merge_of_empty_sketch_is_identity():
     B1, i1 = o1.sketch()
     np.testing.assert_array_equal(B0, B1)
     assert i1["normA2"] == i0["normA2"] and i1["sum_delta"] == i0["sum_delta"]
+
+
+# --------------------------------------------------------------------------
+# Compensative FD (Sec. 3.1) and proj-err (Sec. 1.1)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("variant", ["fd", "pfd"])
+def test_compensative_two_sided_bound(variant):
+    """|x^T (A^T A - B-hat^T B-hat) x| <= Delta for every unit x (Sec. 3.1), and
+    what is added is Delta times the projector onto B's row space (pinv route,
+    independent of the SVD that compensate() takes)."""
+    A = W.random_noisy(700, 40, m=8, seed=81, dtype=np.float64)
+    o = FDOracle(40, 9, variant, _alpha(variant))
+    o.append(A)
+    B, _ = o.sketch()
+    Bh, info = o.sketch_compensated()
+    D = info["sum_delta"]
+    assert D > 0
+    lam = cov_spectrum(A, Bh)
+    assert lam[0] >= -D * (1 + 1e-9) and lam[-1] <= D * (1 + 1e-9), (lam[0], lam[-1], D)
+    P = B.T @ np.linalg.pinv(B @ B.T) @ B
+    np.testing.assert_allclose(Bh.T @ Bh - B.T @ B, D * P, atol=1e-9 * float(np.sum(B * B)))
+
+
+def test_compensative_without_reduction_keeps_the_covariance():
+    """A stream that never reduced has Delta = 0: B-hat^T B-hat = B^T B."""
+    A = W.random_noisy(7, 30, m=4, seed=84, dtype=np.float64)
+    o = FDOracle(30, 9, "fd")
+    o.append(A)
+    B, _ = o.sketch()
+    Bh, info = o.sketch_compensated()
+    assert info["sum_delta"] == 0.0
+    np.testing.assert_allclose(Bh.T @ Bh, B.T @ B, atol=1e-12 * float(np.sum(B * B)))
+    with pytest.raises(ValueError):
+        FDOracle(30, 9, "isvd").sketch_compensated()
+
+
+def test_proj_err_closed_forms():
+    """proj-err of B = A is 1; brute force against an explicit projector (eigh
+    of B^T B) over the tail of A's SVD; never below 1 (Sec. 1.1)."""
+    A = W.random_noisy(600, 30, m=12, seed=82, dtype=np.float64)
+    assert proj_err(A, A, 5) == pytest.approx(1.0, rel=1e-9)
+    rng = np.random.default_rng(85)
+    B = rng.standard_normal((7, 30))
+    _, Q = np.linalg.eigh(B.T @ B)
+    Qk = Q[:, -5:]
+    num = float(np.sum((A - A @ Qk @ Qk.T) ** 2))
+    sv = np.linalg.svd(A, compute_uv=False)
+    den = float(np.sum(sv[5:] ** 2))
+    pe = proj_err(A, B, 5)
+    assert pe == pytest.approx(num / den, rel=1e-9)
+    assert pe >= 1.0 - 1e-12
+    # B of rank 2 < k: B_k spans those two directions only
+    B2 = B[:2]
+    _, Q2 = np.linalg.eigh(B2.T @ B2)
+    Q2 = Q2[:, -2:]
+    num2 = float(np.sum((A - A @ Q2 @ Q2.T) ** 2))
+    assert proj_err(A, B2, 5) == pytest.approx(num2 / den, rel=1e-9)
+
+
+@pytest.mark.parametrize("variant,alpha", [("fd", 1.0), ("pfd", 0.5)])
+def test_proj_err_bounds(variant, alpha):
+    """||A - pi_{B_k}(A)||_F^2 <= alpha ell / (alpha ell - k) ||A - A_k||_F^2
+    (Sec. 3.1); compensative FD keeps V, so its proj-err is the same and within
+    ell / (ell - k)."""
+    A = W.random_noisy(900, 50, m=10, seed=83, dtype=np.float64)
+    ell, k = 16, 4
+    o = FDOracle(50, ell, variant, alpha)
+    o.append(A)
+    B, _ = o.sketch()
+    Bh, _ = o.sketch_compensated()
+    pe = proj_err(A, B, k)
+    assert 1.0 - 1e-12 <= pe <= alpha * ell / (alpha * ell - k), pe
+    peh = proj_err(A, Bh, k)
+    assert peh == pytest.approx(pe, rel=1e-9)
+    assert peh <= ell / (ell - k)
+

@@ -1,0 +1,67 @@
+"""fd_proj_err (Sec. 1.1) vs the FP64 oracle.
+
+Two checks per variant: the evaluator alone (the oracle's proj-err of the
+GPU's own sketch; differences come from FP32 products summed in FP64 in the
+projection pass, about 1e-7 relative), and end to end (against the oracle's
+sketch of the same stream, where the top-k subspace of the FP32 sketch
+itself differs slightly).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import fd_sketch, proj_err
+from paper_1501_06561_gb300 import fd
+from paper_1501_06561_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+EVAL_REL = 1e-6   # evaluator on the same sketch
+E2E_ABS = 1e-4    # whole path vs the oracle's sketch (proj-err is about 1)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    fd.load()
+
+
+@pytest.mark.parametrize("variant,alpha", [("fd", 1.0), ("pfd", 0.4), ("ss", 1.0), ("isvd", 1.0)])
+def test_proj_err_matches_oracle(variant, alpha):
+    """4,001 x 290 Random Noisy stream, ell = 21, k = 10 (the paper's default)."""
+    A = W.random_noisy(4001, 290, m=10, seed=93, dtype=np.float32)
+    Ad = torch.from_numpy(A).cuda()
+    with fd.FDSketch(290, 21, variant, alpha, "fp32") as s:
+        s.append(Ad)
+        B = s.sketch()
+        pe_dev = s.proj_err(Ad, 10)
+        pe_host = s.proj_err(A, 10)
+    pe_same = proj_err(A, B, 10)
+    assert abs(pe_dev - pe_same) <= EVAL_REL * pe_same, (pe_dev, pe_same)
+    assert abs(pe_host - pe_dev) <= 1e-12 * pe_dev
+    Bo, _ = fd_sketch(A, 21, variant, alpha)
+    pe_o = proj_err(A, Bo, 10)
+    assert abs(pe_dev - pe_o) <= E2E_ABS, (pe_dev, pe_o)
+    assert pe_dev >= 1.0 - 1e-6
+
+
+def test_proj_err_sketch_of_low_rank_stream_is_exact():
+    """A stream of rank 6 < ell: the sketch holds A's row space, so B_k = A_k's
+    span and the ratio is 1 (k = 4)."""
+    A = W.random_noisy(500, 64, m=6, zeta=1e30, seed=94, dtype=np.float64)
+    with fd.FDSketch(64, 12, "fd", 1.0, "fp64") as s:
+        s.append(torch.from_numpy(A).cuda())
+        pe = s.proj_err(torch.from_numpy(A).cuda(), 4)
+    assert abs(pe - 1.0) <= 1e-6, pe
+
+
+def test_proj_err_rejects_bad_k():
+    A = torch.zeros((10, 32), dtype=torch.float32, device="cuda")
+    with fd.FDSketch(32, 4) as s:
+        s.append(A + 1.0)
+        for k in (0, 4):
+            with pytest.raises(fd.FDError):
+                s.proj_err(A, k)
