@@ -53,7 +53,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS))
     ap.add_argument("--ell", type=int)
-    ap.add_argument("--variant", choices=["fd", "pfd", "ss", "isvd"])
+    ap.add_argument("--variant", choices=["fd", "pfd", "ss", "isvd", "fastpfd"])
+    ap.add_argument("--buffer-rows", type=int,
+                    help="single stream: rows held before a reduction (default 2*ell; ell for fastpfd)")
     ap.add_argument("--alpha", type=float)
     ap.add_argument("--prec", choices=["fp32", "bf16x3", "fp64"])
     ap.add_argument("--n", type=int)
@@ -79,8 +81,9 @@ def config(args):
         v = getattr(args, k)
         if v is not None:
             w[k] = v
-    if w["variant"] == "pfd" and args.alpha is None:
+    if w["variant"] in ("pfd", "fastpfd") and args.alpha is None:
         w["alpha"] = 0.2
+    w["buffer_rows"] = args.buffer_rows
     return w
 
 
@@ -167,7 +170,7 @@ def cpu_baseline(w, rows_sample):
     A = workloads.random_noisy(rows_sample, w["d"], m=w["m"], zeta=w["zeta"], seed=w["seed"],
                                dtype=np.float32, row_stop=rows_sample)
     t0 = time.perf_counter()
-    fd_sketch(A, w["ell"], w["variant"], w["alpha"])
+    fd_sketch(A, w["ell"], w["variant"], w["alpha"], buffer_rows=w.get("buffer_rows"))
     dt = time.perf_counter() - t0
     try:
         from threadpoolctl import threadpool_info
@@ -233,7 +236,7 @@ def run_reference(args, w):
                                dtype=np.float32, row_stop=rows)
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        fd_sketch(A, w["ell"], w["variant"], w["alpha"])
+        fd_sketch(A, w["ell"], w["variant"], w["alpha"], buffer_rows=w.get("buffer_rows"))
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
     t = sum(times) / len(times)
@@ -533,7 +536,8 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    sk = fd.FDSketch(w["d"], w["ell"], w["variant"], w["alpha"], w["prec"])
+    sk = fd.FDSketch(w["d"], w["ell"], w["variant"], w["alpha"], w["prec"],
+                     buffer_rows=w.get("buffer_rows"))
 
     def step(s, src):
         s.reset()
@@ -593,7 +597,8 @@ def main():
     # plain FP32 CUDA-core update on the same stream, for the matched-error comparison
     plain = None
     if not args.no_plain and w["prec"] != "fp32":
-        sp = fd.FDSketch(w["d"], w["ell"], w["variant"], w["alpha"], "fp32")
+        sp = fd.FDSketch(w["d"], w["ell"], w["variant"], w["alpha"], "fp32",
+                         buffer_rows=w.get("buffer_rows"))
         step(sp, A)
         torch.cuda.synchronize()
         q0 = torch.cuda.Event(enable_timing=True)
@@ -614,7 +619,8 @@ def main():
         P = args.shards
         cuts = [w["n"] * i // P for i in range(P + 1)]
         streams = [torch.cuda.Stream() for _ in range(P)]
-        shs = [fd.FDSketch(w["d"], w["ell"], w["variant"], w["alpha"], w["prec"], stream=st)
+        shs = [fd.FDSketch(w["d"], w["ell"], w["variant"], w["alpha"], w["prec"], stream=st,
+                           buffer_rows=w.get("buffer_rows"))
                for st in streams]
 
         def sharded_run():
@@ -673,6 +679,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": w["name"], "ell": w["ell"], "variant": w["variant"],
                    "alpha": w["alpha"], "prec": w["prec"], "rows_per_step": w["n"],
+                   "buffer_rows": w.get("buffer_rows") or (w["ell"] if w["variant"] == "fastpfd"
+                                                           else 2 * w["ell"]),
                    "input_bytes": int(A_host.nbytes),
                    "l2": "input larger than L2 (no flush needed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

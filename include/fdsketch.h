@@ -46,8 +46,14 @@ extern "C" {
  * are zeroed (Algorithm 2). SS: the second-smallest direction's squared value
  * is added to the smallest and the second-smallest is freed, repeated until
  * ell-1 directions remain; empty directions are freed first (Algorithm 3).
- * ISVD: sigma'_j = sigma_j for j < ell, else 0 (Sec. 2.3). */
-enum { FD_VAR_FD = 0, FD_VAR_PFD = 1, FD_VAR_SS = 2, FD_VAR_ISVD = 3 };
+ * ISVD: sigma'_j = sigma_j for j < ell, else 0 (Sec. 2.3).
+ * FAST_PFD (Fast alpha-FD, Sec. 3.1 "Fast Parameterized FD"): the sketch is
+ * its own ell-row buffer; delta = sigma_t^2 with t = ell - ell*alpha/2
+ * (ell*alpha/2 rounded down, at least 1); the first floor((1-alpha)*ell)
+ * values (at most t-1) are kept and the others become
+ * sqrt(max(sigma_j^2 - delta, 0)), so a reduction leaves t-1 rows and the next
+ * one comes ell-t+1 rows later. Single-sketch handles only (not batched). */
+enum { FD_VAR_FD = 0, FD_VAR_PFD = 1, FD_VAR_SS = 2, FD_VAR_ISVD = 3, FD_VAR_FAST_PFD = 4 };
 
 /* Arithmetic of the reduction.
  * FD_PREC_FP32:   FP32 buffer, FP32 CUDA-core Gram and rotate, FP32 Jacobi
@@ -103,10 +109,20 @@ typedef struct {
 
 /* Create a sketch of width d with ell output rows (fd_sketch returns ell x d;
  * the last row is always zero, as in Algorithm 1 a reduced sketch uses at most
- * ell-1 rows). alpha is used by FD_VAR_PFD only. cuda_stream is a
+ * ell-1 rows). alpha is used by FD_VAR_PFD and FD_VAR_FAST_PFD only. cuda_stream is a
  * cudaStream_t (NULL = the legacy default stream). Allocates all device state. */
 int fd_create(int64_t d, int32_t ell, int32_t variant, double alpha, int32_t prec,
               void* cuda_stream, fd_handle* out);
+
+/* fd_create with the buffer size chosen: buffer_rows rows are held before a
+ * reduction (fd_create uses 2*ell, and ell for FD_VAR_FAST_PFD). For the
+ * other variants 2*ell <= buffer_rows <= FD_MAX_BUFFER_ROWS: delta stays the
+ * ell-th squared singular value of the buffer and a reduction leaves ell-1
+ * rows, so one reduction handles buffer_rows - ell + 1 new rows (the buffer
+ * of Fast FD, Sec. 2.3, taken larger to spread the eigensolve over more rows).
+ * FD_VAR_FAST_PFD requires buffer_rows == ell. FD_EINVAL otherwise. */
+int fd_create_buffered(int64_t d, int32_t ell, int32_t variant, double alpha, int32_t prec,
+                       int32_t buffer_rows, void* cuda_stream, fd_handle* out);
 
 /* Append n rows (Algorithm 1's loop body, "insert a_i", reducing whenever the
  * 2*ell buffer is full). n = 0 is a no-op. Asynchronous for device rows. */

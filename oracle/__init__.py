@@ -11,6 +11,7 @@ from .fd_oracle import (  # noqa: F401
     compensate,
     cov_err,
     cov_spectrum,
+    fast_pfd_split,
     fd_sketch,
     proj_err,
     reduce_rank,

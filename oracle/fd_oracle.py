@@ -53,7 +53,7 @@ import math
 
 import numpy as np
 
-VARIANTS = ("fd", "pfd", "ss", "isvd")
+VARIANTS = ("fd", "pfd", "ss", "isvd", "fastpfd")
 
 
 def shrink_index_split(ell: int, alpha: float) -> int:
@@ -67,6 +67,23 @@ def shrink_index_split(ell: int, alpha: float) -> int:
     keep = int(math.floor((1.0 - alpha) * ell + 1e-9))
     keep = max(0, min(ell - 1, keep))   # alpha > 0: at least one value shrinks
     return ell - keep
+
+
+def fast_pfd_split(ell: int, alpha: float):
+    """``(keep, t)`` of Fast alpha-FD (Sec. 3.1, "Fast Parameterized FD").
+
+    ``delta = sigma_t^2`` with ``t = ell - ell*alpha/2``; the first
+    ``ell(1-alpha)`` values are kept, the others become
+    ``sqrt(max(sigma^2 - delta, 0))``, so values ``t .. ell`` become zero.
+    ``ell*alpha/2`` is rounded down but taken as at least 1, and
+    ``ell(1-alpha)`` is rounded down and capped at ``t-1`` so that at least
+    one value before ``t`` is shrunk; a reduction then leaves ``t-1`` rows.
+    """
+    half = max(1, int(math.floor(alpha * ell / 2.0 + 1e-9)))
+    t = ell - half
+    keep = int(math.floor((1.0 - alpha) * ell + 1e-9))
+    keep = max(0, min(t - 1, keep))
+    return keep, t
 
 
 def reduce_rank(sigma, ell: int, variant: str, alpha: float = 1.0,
@@ -102,6 +119,16 @@ def reduce_rank(sigma, ell: int, variant: str, alpha: float = 1.0,
         delta = sig_ell_sq
         nshrink = shrink_index_split(ell, alpha)
         keep = ell - nshrink
+        sp = np.zeros_like(s)
+        top = min(keep, L)
+        sp[:top] = s[:top]
+        hi = min(ell, L)
+        if hi > keep:
+            sp[keep:hi] = np.sqrt(np.maximum(sq[keep:hi] - delta, 0.0))
+        return sp, [delta]
+    if variant == "fastpfd":
+        keep, t = fast_pfd_split(ell, alpha)
+        delta = sq[t - 1] if L >= t else 0.0
         sp = np.zeros_like(s)
         top = min(keep, L)
         sp[:top] = s[:top]
@@ -161,18 +188,32 @@ class FDOracle:
     """
 
     def __init__(self, d: int, ell: int, variant: str = "fd", alpha: float = 1.0,
-                 mode: str = "buffered", record: bool = False):
+                 mode: str = "buffered", record: bool = False, buffer_rows: int | None = None):
         if variant not in VARIANTS:
             raise ValueError(variant)
         if ell < 2 or d < 1:
             raise ValueError("need ell >= 2 and d >= 1")
-        if variant == "pfd" and not (0.0 < alpha <= 1.0):
+        if variant in ("pfd", "fastpfd") and not (0.0 < alpha <= 1.0):
             raise ValueError("alpha must lie in (0, 1]")
         if mode not in ("buffered", "literal"):
             raise ValueError(mode)
         self.d, self.ell, self.variant, self.mode = d, ell, variant, mode
-        self.alpha = alpha if variant == "pfd" else 1.0
-        self.cap = 2 * ell if mode == "buffered" else ell
+        self.alpha = alpha if variant in ("pfd", "fastpfd") else 1.0
+        if variant == "fastpfd":
+            # the sketch is its own buffer (ell rows); a reduction leaves t-1 rows
+            _, t = fast_pfd_split(ell, self.alpha)
+            if t < 2:
+                raise ValueError("Fast alpha-FD needs ell - ell*alpha/2 >= 2")
+            if buffer_rows not in (None, ell):
+                raise ValueError("Fast alpha-FD uses an ell-row buffer")
+            self.cap, self.keep_rows = ell, t - 1
+        else:
+            # buffered FD: a buffer of c*ell rows (c >= 2; Fast FD of Sec. 2.3
+            # with delta = sigma_ell^2) that always leaves ell-1 rows
+            cap = 2 * ell if buffer_rows is None else int(buffer_rows)
+            if mode == "buffered" and cap < 2 * ell:
+                raise ValueError("the buffer holds at least 2*ell rows")
+            self.cap, self.keep_rows = (cap if mode == "buffered" else ell), ell - 1
         self.buf = np.zeros((self.cap, d))
         self.m = 0                     # buffered: filled rows (zero rows included)
         self.normA2 = 0.0
@@ -239,7 +280,7 @@ class FDOracle:
                 self._commit(deltas, removed)
                 self.buf[:] = 0.0
                 self.buf[:new_rows.shape[0]] = new_rows
-                self.m = self.ell - 1
+                self.m = self.keep_rows
 
     def _append_literal(self, a):
         self.normA2 += float(np.dot(a, a))
@@ -326,13 +367,13 @@ class FDOracle:
 
 
 def fd_sketch(A, ell: int, variant: str = "fd", alpha: float = 1.0,
-              mode: str = "buffered", record: bool = False):
+              mode: str = "buffered", record: bool = False, buffer_rows: int | None = None):
     """Run the whole stream ``A`` (rows in order) and return ``(B, info)``.
 
     With ``record=True`` the per-reduction records are in ``info["records"]``.
     """
     A = np.asarray(A)
-    o = FDOracle(A.shape[1], ell, variant, alpha, mode, record)
+    o = FDOracle(A.shape[1], ell, variant, alpha, mode, record, buffer_rows)
     o.append(A)
     B, info = o.sketch()
     if record:

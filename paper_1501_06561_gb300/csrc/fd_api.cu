@@ -37,7 +37,7 @@ size_t tri_global_workspace(int n);
 
 // tensor-core path (fd_tc.cu)
 struct TcCtx;
-int tc_create(TcCtx** out, int64_t d, int ell, cudaStream_t st);
+int tc_create(TcCtx** out, int64_t d, int ell, int L, cudaStream_t st);
 void tc_destroy(TcCtx* t);
 int tc_ingest(TcCtx* t, const void* src, int64_t n, int64_t ld, int dtype, int row0,
               double* rownorm, DevCounters* ctr);
@@ -78,6 +78,7 @@ struct fd_state {
   void* parts = nullptr;  // Gram partial slices
   int ldp = 0;
   int ksplit = 1;
+  int keep = 0;  // rows a reduction leaves in the buffer
   void* work = nullptr;   // eigensolve matrix in global memory when it does not fit smem
   size_t work_bytes = 0;
   void* wrot = nullptr;   // rotate matrix (ell-1) x ldr
@@ -185,10 +186,26 @@ extern "C" int fd_create(int64_t d, int32_t ell, int32_t variant, double alpha, 
                          void* cuda_stream, fd_handle* out) {
   if (!out) return FD_EINVAL;
   *out = nullptr;
-  if (d < 1 || ell < 2 || 2 * (int64_t)ell > FD_MAX_BUFFER_ROWS) return FD_EINVAL;
-  if (variant < FD_VAR_FD || variant > FD_VAR_ISVD) return FD_EINVAL;
+  if (ell < 2 || 2 * (int64_t)ell > FD_MAX_BUFFER_ROWS) return FD_EINVAL;
+  return fd_create_buffered(d, ell, variant, alpha, prec,
+                            variant == FD_VAR_FAST_PFD ? ell : 2 * ell, cuda_stream, out);
+}
+
+extern "C" int fd_create_buffered(int64_t d, int32_t ell, int32_t variant, double alpha,
+                                  int32_t prec, int32_t buffer_rows, void* cuda_stream,
+                                  fd_handle* out) {
+  if (!out) return FD_EINVAL;
+  *out = nullptr;
+  if (d < 1 || ell < 2 || buffer_rows > FD_MAX_BUFFER_ROWS) return FD_EINVAL;
+  if (variant < FD_VAR_FD || variant > FD_VAR_FAST_PFD) return FD_EINVAL;
   if (prec < FD_PREC_FP32 || prec > FD_PREC_FP64) return FD_EINVAL;
-  if (variant == FD_VAR_PFD && !(alpha > 0.0 && alpha <= 1.0)) return FD_EINVAL;
+  if ((variant == FD_VAR_PFD || variant == FD_VAR_FAST_PFD) && !(alpha > 0.0 && alpha <= 1.0))
+    return FD_EINVAL;
+  if (variant == FD_VAR_FAST_PFD) {
+    if (buffer_rows != ell || fast_pfd_t(ell, alpha) < 2) return FD_EINVAL;
+  } else if (buffer_rows < 2 * ell) {
+    return FD_EINVAL;
+  }
   if (prec == FD_PREC_BF16X3 && !tc_available()) return FD_EINVAL;
 
   fd_state* h = new (std::nothrow) fd_state();
@@ -196,9 +213,12 @@ extern "C" int fd_create(int64_t d, int32_t ell, int32_t variant, double alpha, 
   h->d = d;
   h->ldb = (d + 63) / 64 * 64;
   h->ell = ell;
-  h->L = 2 * ell;
+  h->L = buffer_rows;
+  // rows a reduction leaves: ell-1, or t-1 for Fast alpha-FD (its values
+  // t..ell are zeroed, so the next t-1.. slots are free)
+  h->keep = (variant == FD_VAR_FAST_PFD) ? fast_pfd_t(ell, alpha) - 1 : ell - 1;
   h->variant = variant;
-  h->alpha = (variant == FD_VAR_PFD) ? alpha : 1.0;
+  h->alpha = (variant == FD_VAR_PFD || variant == FD_VAR_FAST_PFD) ? alpha : 1.0;
   h->prec = prec;
   h->st = reinterpret_cast<cudaStream_t>(cuda_stream);
   h->es = (prec == FD_PREC_FP64) ? 8 : 4;
@@ -236,7 +256,7 @@ extern "C" int fd_create(int64_t d, int32_t ell, int32_t variant, double alpha, 
       wb = std::max(wb, tri_global_workspace(h->L));
     if (wb) { FD_ALLOC(h->work, wb); h->work_bytes = wb; }
   } else {
-    int rc = tc_create(&h->tc, d, ell, h->st);
+    int rc = tc_create(&h->tc, d, ell, h->L, h->st);
     if (rc != FD_OK) { free_state(h); return rc; }
     size_t wb = eig_fits_smem(h->L, 4) ? 0 : (size_t)(np + 1) * (np + 1) * 4;
     if (tri_config(h->L, ell) == 4) wb = std::max(wb, tri_global_workspace(h->L));
@@ -294,7 +314,7 @@ static int reduce_rows(fd_state* h, int nrows, void* out, int64_t ldo, DevCounte
   a.max_sweeps = h->max_sweeps;
   a.tol = h->tol;
   a.symmetrize = 1;
-  a.use_tri = 1;
+  a.use_tri = (nrows == h->L) ? 1 : 0;  // flushes of a partial buffer keep Jacobi
   if (h->prec == FD_PREC_BF16X3) {
     int rc;
     { ProfScope ps(h, FD_K_GRAM); rc = tc_gram(h->tc, nrows); }
@@ -367,7 +387,7 @@ static int append_device(fd_state* h, const char* src, int64_t n, int64_t ld, in
         h->cur = nxt;
       }
       if (rc != FD_OK) return rc;
-      h->m = h->ell - 1;
+      h->m = h->keep;
     }
   }
   return FD_OK;

@@ -73,12 +73,19 @@ static __device__ void shrink_sorted(const EigArgs& a, int n, int np, double eps
   // 5. ReduceRank in FP64 on the masses mu_k = sigma_k^2 (k = 0..n-1 sorted).
   const int ell = a.ell;
   if (a.variant != FD_VAR_SS) {
-    const double delta = (n >= ell) ? mu[ell - 1] : 0.0;
+    double delta = (n >= ell) ? mu[ell - 1] : 0.0;
     int keep = 0;
     if (a.variant == FD_VAR_PFD) {
       // Algorithm 2 keeps floor((1-alpha)*ell) values; alpha > 0 shrinks at least one
       keep = (int)floor((1.0 - a.alpha) * ell + 1e-9);
       keep = keep < 0 ? 0 : (keep > ell - 1 ? ell - 1 : keep);
+    } else if (a.variant == FD_VAR_FAST_PFD) {
+      // Fast alpha-FD: delta = sigma_t^2, t = ell - ell*alpha/2 (at least one
+      // value past t); floor((1-alpha)*ell) values kept, at most t-1
+      const int t = fast_pfd_t(ell, a.alpha);
+      keep = (int)floor((1.0 - a.alpha) * ell + 1e-9);
+      keep = keep < 0 ? 0 : (keep > t - 1 ? t - 1 : keep);
+      delta = (n >= t) ? mu[t - 1] : 0.0;
     }
     for (int k = tid; k < np; k += blockDim.x) {
       const double m0 = mu[k];
@@ -86,6 +93,7 @@ static __device__ void shrink_sorted(const EigArgs& a, int n, int np, double eps
       if (k < n) {
         if (a.variant == FD_VAR_FD) mp = fmax(m0 - delta, 0.0);
         else if (a.variant == FD_VAR_ISVD) mp = (k < ell - 1) ? m0 : 0.0;
+        // PFD and Fast alpha-FD: keep, then clip at zero up to ell, zero past it
         else mp = (k < keep) ? m0 : ((k < ell) ? fmax(m0 - delta, 0.0) : 0.0);
       }
       mup[k] = mp;

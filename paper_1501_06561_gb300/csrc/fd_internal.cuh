@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <math.h>
 
 #include "fdsketch.h"
 
@@ -52,6 +53,14 @@ struct EigArgs {
   int use_tri;         // 1: tridiagonal eigensolve where it applies (FP32)
   double* row_mass;    // optional: sigma'^2 of each output row r (ell-1 entries)
 };
+
+// t of Fast alpha-FD (Sec. 3.1): delta = sigma_t^2, t = ell - ell*alpha/2 with
+// ell*alpha/2 rounded down and at least 1.
+__host__ __device__ inline int fast_pfd_t(int ell, double alpha) {
+  int half = (int)floor(alpha * ell / 2.0 + 1e-9);
+  if (half < 1) half = 1;
+  return ell - half;
+}
 
 // --- launchers (fd_simt.cu) -------------------------------------------------
 cudaError_t launch_ingest(const void* src, int64_t n, int64_t ld, int dtype,

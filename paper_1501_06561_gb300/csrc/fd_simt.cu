@@ -358,13 +358,14 @@ cudaError_t launch_tri(const EigArgs& a, size_t smem, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Whether a reduction of n rows takes the tridiagonal eigensolve: full
-// buffers only (flushes of a partial buffer keep Jacobi). 1: n <= 128 in
+// Whether a reduction of n rows takes the tridiagonal eigensolve: buffers of
+// at least 2*ell rows (the caller passes use_tri only for full buffers;
+// flushes of a partial buffer keep Jacobi). 1: n <= 128 in
 // shared memory; 2, 3: up to 206 rows in shared memory (LU batches of 16 or 8
 // vectors for the fallback path); 4: up to 512 rows with A and the scratch
 // area in a global workspace of tri_global_bytes(n, 16) bytes.
 int tri_config(int n, int ell) {
-  if (n != 2 * ell || n < 4) return 0;
+  if (n < 2 * ell || n < 4) return 0;  // retained vectors <= n/2
   const size_t rw = tri_rw_bytes(n, 16);  // 512 threads
   if (n <= 128 && tri_smem_bytes(n, 32) <= 226 * 1024 && tri_scratch_bytes(n, 32) >= rw) return 1;
   if (n <= 208 && tri_smem_bytes(n, 16) <= 226 * 1024 && tri_scratch_bytes(n, 16) >= rw) return 2;

@@ -6,7 +6,7 @@
 // A product x*y is taken as hi_x*hi_y + hi_x*lo_y + lo_x*hi_y (the lo*lo term,
 // about 2^-16 of the product, is dropped) and accumulated in FP32.
 //
-// Buffer layout in HBM (one sketch of width d, buffer L = 2*ell rows):
+// Buffer layout in HBM (one sketch of width d, buffer of L rows, L = 2*ell by default):
 //   rm_hi, rm_lo2: row-major  L x ldb  (ldb = d rounded up to 64), lo2 = 2*lo
 //   cm_hi, cm_lo:  column-major (d x L stored as ldb rows of ldl, ldl = L up
 //                  to a multiple of 64)
@@ -470,14 +470,14 @@ void tc_destroy(TcCtx* t) {
   delete t;
 }
 
-int tc_create(TcCtx** out, int64_t d, int ell, cudaStream_t st) {
+int tc_create(TcCtx** out, int64_t d, int ell, int L, cudaStream_t st) {
   *out = nullptr;
   TcCtx* t = new (std::nothrow) TcCtx();
   if (!t) return FD_ENOMEM;
   t->d = d;
   t->ldb = (d + 63) / 64 * 64;
   t->ell = ell;
-  t->L = 2 * ell;
+  t->L = L;
   t->ldl = (t->L + 63) / 64 * 64;
   t->Np = ((ell - 1) + 15) / 16 * 16;
   if (t->Np < 16) t->Np = 16;

@@ -18,7 +18,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfdsketch.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "fdsketch.h")
 
-VARIANT = {"fd": 0, "pfd": 1, "ss": 2, "isvd": 3}
+VARIANT = {"fd": 0, "pfd": 1, "ss": 2, "isvd": 3, "fastpfd": 4}
 PREC = {"fp32": 0, "bf16x3": 1, "fp64": 2}
 F32, BF16, F64 = 0, 1, 2
 ERR = {0: "FD_OK", -1: "FD_EINVAL", -2: "FD_ENOMEM", -3: "FD_ECUDA", -4: "FD_ENOCONV",
@@ -61,6 +61,7 @@ def load():
     vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
     sig = {
         "fd_create": [i64, i32, i32, dbl, i32, vp, ctypes.POINTER(vp)],
+        "fd_create_buffered": [i64, i32, i32, dbl, i32, i32, vp, ctypes.POINTER(vp)],
         "fd_append": [vp, vp, i64, i64, i32, i32],
         "fd_sketch": [vp, vp, i32, i32],
         "fd_sketch_compensated": [vp, vp, i32, i32],
@@ -158,13 +159,18 @@ class FDSketch:
     """One buffered FD sketch on the GPU (fd_create ... fd_destroy)."""
 
     def __init__(self, d: int, ell: int, variant: str = "fd", alpha: float = 1.0,
-                 prec: str = "fp32", stream=None):
+                 prec: str = "fp32", stream=None, buffer_rows: int | None = None):
         lib = load()
         self.d, self.ell, self.variant, self.prec = d, ell, variant, prec
         self._stream = _stream_ptr(stream)
         h = ctypes.c_void_p()
-        _check(lib.fd_create(d, ell, VARIANT[variant], float(alpha), PREC[prec], self._stream,
-                             ctypes.byref(h)), "fd_create")
+        if buffer_rows is None:
+            _check(lib.fd_create(d, ell, VARIANT[variant], float(alpha), PREC[prec], self._stream,
+                                 ctypes.byref(h)), "fd_create")
+        else:
+            _check(lib.fd_create_buffered(d, ell, VARIANT[variant], float(alpha), PREC[prec],
+                                          int(buffer_rows), self._stream, ctypes.byref(h)),
+                   "fd_create_buffered")
         self._h = h
 
     def append(self, rows):

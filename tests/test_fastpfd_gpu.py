@@ -1,0 +1,84 @@
+"""Fast alpha-FD (FD_VAR_FAST_PFD, Sec. 3.1) and buffers of c*ell rows
+(fd_create_buffered) vs the FP64 oracle, through the C ABI.
+
+Same bar as the other parity tests: sketch singular values per the per-value
+allowance, cov-err within 1e-5 absolute, FP64 counters close to the oracle's.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import FDOracle, cov_err, fast_pfd_split
+from paper_1501_06561_gb300 import fd
+from paper_1501_06561_gb300 import workloads as W
+from helpers import COV_ABS, assert_sigma_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    fd.load()
+
+
+def _run(A, ell, variant, alpha, prec, buffer_rows=None):
+    with fd.FDSketch(A.shape[1], ell, variant, alpha, prec, buffer_rows=buffer_rows) as s:
+        s.append(torch.from_numpy(np.ascontiguousarray(A)).cuda())
+        B = s.sketch()
+        st = s.stats()
+    o = FDOracle(A.shape[1], ell, variant, alpha, buffer_rows=buffer_rows)
+    o.append(A)
+    Bo, io = o.sketch()
+    return B, st, Bo, io
+
+
+def _check(A, B, st, Bo, io, prec, what):
+    assert st["n_seen"] == A.shape[0]
+    assert abs(st["norm_a2"] - io["normA2"]) <= 1e-12 * io["normA2"]
+    assert_sigma_parity(B, Bo, io["normA2"], prec, what=what)
+    ce_g, ce_o = cov_err(A, B), cov_err(A, Bo)
+    assert abs(ce_g - ce_o) <= COV_ABS, (what, ce_g, ce_o)
+    assert abs(st["sketch_sum_delta"] - io["sum_delta"]) <= 1e-4 * io["sum_delta"]
+    assert st["noconv"] == 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("ell,alpha", [(21, 0.2), (40, 0.5), (24, 1.0)])
+def test_fast_alpha_fd_matches_oracle(ell, alpha, prec):
+    """4,001 x 290 Random Noisy stream; Fast 0.2-FD is the paper's experimental
+    variant. With alpha = 0.2, ell = 21 a reduction comes every 3 rows."""
+    A = W.random_noisy(4001, 290, m=10, seed=95, dtype=np.float32)
+    B, st, Bo, io = _run(A, ell, "fastpfd", alpha, prec)
+    keep, t = fast_pfd_split(ell, alpha)
+    assert st["reductions"] == io["reductions"] == (4001 - ell) // (ell - t + 1) + 1
+    _check(A, B, st, Bo, io, prec, f"fastpfd ell={ell} alpha={alpha} {prec}")
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("variant,alpha", [("fd", 1.0), ("pfd", 0.4), ("isvd", 1.0)])
+@pytest.mark.parametrize("factor", [3, 4])
+def test_larger_buffer_matches_oracle(variant, alpha, prec, factor):
+    """ell = 21 with a buffer of 63 or 84 rows (the tridiagonal eigensolve on
+    a full buffer of more than 2*ell rows); a ragged flush at the end."""
+    A = W.random_noisy(4001, 290, m=10, seed=96, dtype=np.float32)
+    L = factor * 21
+    B, st, Bo, io = _run(A, 21, variant, alpha, prec, buffer_rows=L)
+    assert st["reductions"] == (4001 - L) // (L - 20) + 1
+    _check(A, B, st, Bo, io, prec, f"{variant} L={L} {prec}")
+
+
+def test_bad_buffer_arguments():
+    with pytest.raises(fd.FDError):
+        fd.FDSketch(64, 10, "fastpfd", 0.2, buffer_rows=20)   # Fast alpha-FD: ell rows
+    with pytest.raises(fd.FDError):
+        fd.FDSketch(64, 10, "fd", 1.0, buffer_rows=19)        # below 2*ell
+    with pytest.raises(fd.FDError):
+        fd.FDSketch(64, 10, "fd", 1.0, buffer_rows=513)       # above the limit
+    with pytest.raises(fd.FDError):
+        fd.FDSketch(64, 10, "fastpfd", 0.0)                   # alpha outside (0, 1]
+    with pytest.raises(fd.FDError):
+        fd.FDBatch([64, 64], [8, 8], "fastpfd", 0.2)          # single sketches only

@@ -16,15 +16,16 @@ import os
 import numpy as np
 import pytest
 
-from oracle import FDOracle, compensate, cov_err, cov_spectrum, fd_sketch, proj_err, reduce_rank
+from oracle import (FDOracle, compensate, cov_err, cov_spectrum, fast_pfd_split, fd_sketch,
+                    proj_err, reduce_rank)
 from paper_1501_06561_gb300 import workloads as W
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-VARS = ["fd", "pfd", "ss", "isvd"]
+VARS = ["fd", "pfd", "ss", "isvd", "fastpfd"]
 
 
 def _alpha(v):
-    return 0.5 if v == "pfd" else 1.0
+    return {"pfd": 0.5, "fastpfd": 0.4}.get(v, 1.0)
 
 
 # --------------------------------------------------------------------------
@@ -56,7 +57,8 @@ def _cov_replay(A, ell, variant, alpha, mode):
     """
     d = A.shape[1]
     C = np.zeros((d, d))
-    cap = 2 * ell if mode == "buffered" else ell
+    cap = 2 * ell if (mode == "buffered" and variant != "fastpfd") else ell
+    left = ell - 1 if variant != "fastpfd" else fast_pfd_split(ell, alpha)[1] - 1
     rows = 0
     sum_delta = 0.0
 
@@ -77,7 +79,7 @@ def _cov_replay(A, ell, variant, alpha, mode):
         if rows == cap:
             C, deltas, nz = reduce(C, rows)
             sum_delta += sum(deltas)
-            rows = ell - 1 if mode == "buffered" else nz
+            rows = left if mode == "buffered" else nz
     if mode == "buffered" and rows > ell - 1:
         C, deltas, _ = reduce(C, rows)
         sum_delta += sum(deltas)
@@ -108,7 +110,9 @@ def test_covariance_form_replay(variant, mode):
 @pytest.mark.parametrize("mode", ["buffered", "literal"])
 def test_exact_recovery_low_rank(variant, mode):
     ell = 6
-    A = W.low_rank_rows(300, 20, rank=ell - 1)
+    # Fast alpha-FD keeps t-1 rows, so exact recovery needs rank <= t-1
+    rank = ell - 1 if variant != "fastpfd" else fast_pfd_split(ell, _alpha(variant))[1] - 1
+    A = W.low_rank_rows(300, 20, rank=rank)
     B, info = fd_sketch(A, ell, variant, _alpha(variant), mode)
     lam = cov_spectrum(A, B)
     assert max(abs(lam[0]), abs(lam[-1])) <= 1e-10 * info["normA2"]
@@ -118,7 +122,7 @@ def test_exact_recovery_low_rank(variant, mode):
 # --------------------------------------------------------------------------
 # Properties 1-2 and Lemma 1 (per reduction), Property 3 / Lemma 3
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("variant", ["fd", "pfd", "isvd"])
+@pytest.mark.parametrize("variant", ["fd", "pfd", "isvd", "fastpfd"])
 @pytest.mark.parametrize("mode", ["buffered", "literal"])
 def test_properties_1_2(variant, mode):
     A = W.random_noisy(700, 24, m=6, seed=3, dtype=np.float64)
@@ -129,7 +133,7 @@ def test_properties_1_2(variant, mode):
     assert lam[-1] <= info["sum_delta"] + tol   # Property 2
 
 
-@pytest.mark.parametrize("variant", ["fd", "pfd", "isvd"])
+@pytest.mark.parametrize("variant", ["fd", "pfd", "isvd", "fastpfd"])
 @pytest.mark.parametrize("mode", ["buffered", "literal"])
 def test_lemma1_each_reduction(variant, mode):
     A = W.random_noisy(200, 16, m=5, seed=4, dtype=np.float64)
@@ -436,4 +440,61 @@ def test_proj_err_bounds(variant, alpha):
     peh = proj_err(A, Bh, k)
     assert peh == pytest.approx(pe, rel=1e-9)
     assert peh <= ell / (ell - k)
+
+
+# --------------------------------------------------------------------------
+# Fast alpha-FD (Sec. 3.1) and buffers of c*ell rows
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("ell,alpha", [(20, 0.2), (12, 0.5), (10, 1.0)])
+@pytest.mark.parametrize("mode", ["buffered", "literal"])
+def test_fast_alpha_fd_bounds(ell, alpha, mode):
+    """Each reduction removes delta from the values keep .. t (t - keep of
+    them, at least alpha*ell/2) and at most delta from any direction, so
+    ||A||^2 - ||B||^2 >= (t - keep) Delta, 0 <= x^T (A^T A - B^T B) x <= Delta, and
+    Delta <= ||A - A_k||^2 / ((t - keep) - k): the bound the paper states for
+    ell = 2(k + 1/eps)/alpha. A reduction leaves t-1 rows."""
+    keep, t = fast_pfd_split(ell, alpha)
+    assert t - keep >= alpha * ell / 2 - 1e-12
+    A = W.random_noisy(1500, 50, m=12, seed=87, dtype=np.float64)
+    o = FDOracle(50, ell, "fastpfd", alpha, mode, record=True)
+    o.append(A)
+    B, info = o.sketch()
+    assert info["reductions"] > 10
+    for r in o.records:
+        assert int(np.sum(r["sigma_prime"] > 0)) <= t - 1
+    lhs = info["normA2"] - info["normB2"]
+    D = info["sum_delta"]
+    assert lhs >= (t - keep) * D * (1 - 1e-12)
+    lam = cov_spectrum(A, B)
+    tol = 1e-10 * info["normA2"]
+    assert lam[0] >= -tol and lam[-1] <= D + tol
+    s = np.linalg.svd(A, compute_uv=False)
+    for k in range(0, t - keep):
+        tail = float(np.sum(s[k:] ** 2))
+        assert D <= tail / ((t - keep) - k) * (1 + 1e-10), (k, D, tail)
+
+
+@pytest.mark.parametrize("variant", ["fd", "pfd", "ss", "isvd"])
+def test_larger_buffer(variant):
+    """A buffer of 3*ell rows: the same index rules, a reduction every 2*ell+1
+    rows; FD's guarantees hold as for 2*ell, and a stream of rank below ell is
+    recovered exactly."""
+    ell = 6
+    A = W.random_noisy(700, 24, m=6, seed=88, dtype=np.float64)
+    o = FDOracle(24, ell, variant, _alpha(variant), buffer_rows=3 * ell)
+    o.append(A)
+    B, info = o.sketch()
+    assert info["reductions"] == 1 + (700 - 3 * ell) // (2 * ell + 1) + 1  # + the flush
+    lam = cov_spectrum(A, B)
+    tol = 1e-10 * info["normA2"]
+    if variant != "isvd":
+        assert lam[-1] <= info["sum_delta"] + tol
+    if variant != "ss":
+        assert lam[0] >= -tol
+    L = W.low_rank_rows(300, 20, rank=ell - 1)
+    o = FDOracle(20, ell, variant, _alpha(variant), buffer_rows=3 * ell)
+    o.append(L)
+    B, info = o.sketch()
+    lam = cov_spectrum(L, B)
+    assert max(abs(lam[0]), abs(lam[-1])) <= 1e-10 * info["normA2"]
 
