@@ -8,7 +8,8 @@
 //      pass over the trailing block (the next reflector is formed from the
 //      updated column first), so each step costs one read and one write of
 //      the trailing block and two barriers. Reflector vectors are packed, in
-//      step order, into the finished leading rows of the same buffer.
+//      step order, into the finished leading rows of the same buffer. The
+//      last 32 steps run on one warp with the block in registers.
 //   2. All eigenvalues of T from Sturm counts of T - x I (LDL^T pivots):
 //      one count per thread on an even grid brackets every eigenvalue, then
 //      groups of lanes refine each bracket by multisection. Values at or
@@ -208,6 +209,65 @@ __device__ __forceinline__ int tri_div14(int a, int b) {
   return (b == 1) ? a : (b == 2) ? (a >> 1) : (b == 4) ? (a >> 2) : a / 3;
 }
 
+// The last steps (trailing block of m0 <= 32) on warp 0 alone, with no block
+// barriers. Lane j holds column s0+1+j of the block in registers (a[i] = row
+// s0+1+i). Entry state is that of the block-wide loop at the top of step s0:
+// the block still lacks step s0-1's update, which Pc carries as (v, q) per
+// row, and Pc[r].z is x_{s0}. At step s0+k the column x_s is, by symmetry,
+// row s of the block: register a[k-1] of every lane. v_i and q_i of other
+// rows come by shuffle from lane i. Writes e, d (from s0+1) and the packed
+// reflectors; the shared-memory copy of the block is left stale.
+__device__ __forceinline__ void tri_reduce_tail(float* A, int ld, int n, int s0, const float4* Pc,
+                                                float* d, float* e) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int j = threadIdx.x & 31;
+  const int m0 = n - 1 - s0;
+  const bool lj = j < m0;
+  const float4 pj = Pc[lj ? j : 0];
+  const float vj = lj ? pj.x : 0.f, qj = lj ? pj.y : 0.f;
+  float x = lj ? pj.z : 0.f;
+  const float* T = A + (size_t)(s0 + 1) * ld + (s0 + 1);
+  float a[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    float v = 0.f;
+    if (i < m0 && lj) {
+      const float4 pi = Pc[i];
+      v = fmaf(-pi.x, qj, fmaf(-pi.y, vj, T[(size_t)i * ld + j]));
+    }
+    a[i] = v;
+  }
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k >= m0) break;
+    const int s = s0 + k, m = m0 - k;
+    if (k > 0) x = a[k - 1];
+    if (j < k) x = 0.f;
+    const float x0 = __shfl_sync(FULL, x, k);
+    const float ss = warp_sum(x * x);
+    float alpha = x0, scale = 0.f;  // a length-1 (or zero) column needs no reflection
+    if (m > 1 && ss > 0.f) {
+      const float nx = sqrtf(ss);
+      alpha = (x0 >= 0.f) ? -nx : nx;
+      scale = 1.f / sqrtf(2.f * (ss - x0 * alpha));
+    }
+    if (j == 0) e[s] = alpha;
+    const float v = (j >= k) ? ((j == k) ? x - alpha : x) * scale : 0.f;
+    if (m > 1 && j >= k) A[tri_voff(n, s) + (j - k)] = v;
+    float p = 0.f;
+#pragma unroll
+    for (int i = k; i < 32; ++i) p = fmaf(a[i], __shfl_sync(FULL, v, i), p);
+    const float K = warp_sum(v * p);
+    const float q = (j >= k) ? 2.f * fmaf(-K, v, p) : 0.f;
+#pragma unroll
+    for (int i = k; i < 32; ++i) {
+      const float vi = __shfl_sync(FULL, v, i), qi = __shfl_sync(FULL, q, i);
+      a[i] = fmaf(-vi, q, fmaf(-qi, v, a[i]));
+    }
+    if (j == k) d[s + 1] = a[k];
+  }
+}
+
 static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, unsigned char* rw,
                                   float* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -233,6 +293,11 @@ static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, u
     const int m = n - 1 - s;  // length of x_s = size of the trailing block
     const float4* Pc = (s & 1) ? P1 : P0;
     float4* Pn = (s & 1) ? P0 : P1;
+    if (m <= 32) {  // the rest on one warp, in registers
+      if (warp == 0) tri_reduce_tail(A, ld, n, s, Pc, d, e);
+      __syncthreads();
+      return;
+    }
     // reflector s: v = (x - alpha e_1) / ||x - alpha e_1||, alpha = -sign(x_0) ||x||
     const float ss = tri_sum_parts(npart, nw);
     const float x0 = Pc[0].z;
@@ -298,7 +363,7 @@ static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, u
     }
     __syncthreads();
   }
-  if (tid == 0) d[n - 1] = A[(size_t)(n - 1) * ld + (n - 1)];
+  if (tid == 0) d[n - 1] = A[(size_t)(n - 1) * ld + (n - 1)];  // n == 1 only
   __syncthreads();
 }
 
