@@ -44,6 +44,17 @@ WORKLOADS = {
 }
 FP32_LANES_PER_SM = 128
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
+# kernel from one full ncu capture, reported as roofline "traffic" only for
+# the configuration it was taken on; None once that kernel changes.
+# Single stream: bytes per eigensolve launch, keyed by (ell, prec, variant,
+# buffer rows); profiles/eig_gram_rotate_c1_ell100_full.md.
+EIG_TRAFFIC = {(100, "bf16x3", "fd", 200): 474368}
+# Batched: DRAM bytes per byte of input rows, from a 64-sketch launch of the
+# same generator (1,860,355,824 B for 1,817,569,744 B of rows), scaled by the
+# rows a launch reads; profiles/batch_kernel_c3_64sketch_full.md.
+BATCH_TRAFFIC_PER_INPUT_BYTE = 1860355824 / 1817569744
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -373,9 +384,13 @@ def run_batch(args, w):
         r = batch_reductions(sp["n"], sp["ell"])
         flops += r * (9.0 * L ** 3 + 2.0 * L * L * sp["d"] + 2.0 * (sp["ell"] - 1) * L * sp["d"])
     achieved = flops / (ms_kernel / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "batch_kernel (persistent: ingest, Gram, Jacobi, "
-                "shrink, rotate per sketch)", "achieved": achieved, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+    in_bytes = int(flat.numel() * flat.element_size())
+    traffic = (int(BATCH_TRAFFIC_PER_INPUT_BYTE * in_bytes)
+               if BATCH_TRAFFIC_PER_INPUT_BYTE and args.workload == "c3" else None)
+    roofline = {"bound": "alu", "kernel": "batch_kernel (persistent: ingest, Gram, tridiagonal "
+                "eigensolve, shrink, rotate per sketch)", "achieved": achieved, "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": traffic,
+                "traffic_source": "ncu capture of 64 sketches, scaled by input bytes",
                 "peak_source": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
                 "algorithmic_flops_per_launch": flops, "avg_launch_us": ms_kernel * 1e3,
                 "hbm_bytes_per_launch": int(flat.numel() * flat.element_size())}
@@ -654,15 +669,22 @@ def main():
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     alu_peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FP32 FMA
     n_eig, ms_eig = ktimes["eig"]
-    L = 2 * w["ell"]
+    L = w.get("buffer_rows") or (w["ell"] if w["variant"] == "fastpfd" else 2 * w["ell"])
     eig_flops = 9.0 * L ** 3  # textbook dense symmetric eigensolve with vectors
     achieved = (eig_flops / (ms_eig / max(n_eig, 1) / 1e3)) / 1e12 if n_eig else None
+    sm_peak = alu_peak / nsm
     roofline = {"bound": "alu", "kernel": "eigensolve + shrink (one CTA per reduction)",
                 "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": (achieved / alu_peak) if achieved else None, "traffic": None,
+                "frac": (achieved / alu_peak) if achieved else None,
+                "traffic": EIG_TRAFFIC.get((w["ell"], w["prec"], w["variant"], L)),
+                "traffic_source": "ncu capture, DRAM bytes per eigensolve launch",
                 "peak_source": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
                 "algorithmic_flops_per_launch": eig_flops,
-                "avg_launch_us": (ms_eig / n_eig * 1e3) if n_eig else None}
+                "avg_launch_us": (ms_eig / n_eig * 1e3) if n_eig else None,
+                # the reductions of one stream form a serial chain, so each
+                # eigensolve runs on one SM: its share of the chip's peak
+                "per_sm": {"peak": sm_peak,
+                           "frac": (achieved / sm_peak) if achieved else None}}
     kshare = {k: {"launches": c, "ms_per_step": m / args.steps,
                   "share": (m / sum(x for _, x in ktimes.values())) if ktimes else None}
               for k, (c, m) in ktimes.items()}
