@@ -268,6 +268,19 @@ __device__ __forceinline__ void tri_reduce_tail(float* A, int ld, int n, int s0,
   }
 }
 
+// Reflector of a column x with ||x||^2 = ss and first entry x0 (length m):
+// alpha = -sign(x0) ||x||, scale = 1 / ||x - alpha e_1||; a length-1 (or
+// zero) column needs no reflection (alpha = x0, scale = 0).
+__device__ __forceinline__ float4 tri_reflector(float ss, float x0, int m) {
+  float alpha = x0, scale = 0.f;
+  if (m > 1 && ss > 0.f) {
+    const float nx = sqrtf(ss);
+    alpha = (x0 >= 0.f) ? -nx : nx;
+    scale = 1.f / sqrtf(2.f * (ss - x0 * alpha));
+  }
+  return make_float4(alpha, scale, x0 - alpha, 0.f);
+}
+
 static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, unsigned char* rw,
                                   float* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -275,18 +288,17 @@ static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, u
   float4* P0 = reinterpret_cast<float4*>(rw);
   float4* P1 = reinterpret_cast<float4*>(rw + tri_al16((size_t)n * 16));
   float* pp = reinterpret_cast<float*>(rw + 2 * tri_al16((size_t)n * 16));
-  float* kpart = red;       // per-warp parts of K = v^T p
-  float* npart = red + 32;  // per-warp parts of ||x||^2
+  float* kpart = red;                                  // per-warp parts of K = v^T p
+  float4* scal = reinterpret_cast<float4*>(red + 32);  // (alpha, scale, x0 - alpha) of the step
   if (tid == 0) d[0] = A[0];
-  {
+  for (int i = tid; i < n - 1; i += nt)
+    P0[i] = make_float4(0.f, 0.f, A[(size_t)(i + 1) * ld], 0.f);  // no previous step to apply
+  __syncthreads();
+  if (warp == 0 && n - 1 > 32) {
     float sq = 0.f;
-    for (int i = tid; i < n - 1; i += nt) {
-      const float x = A[(size_t)(i + 1) * ld];
-      P0[i] = make_float4(0.f, 0.f, x, 0.f);  // no previous step to apply
-      sq = fmaf(x, x, sq);
-    }
-    sq = warp_sum(sq);
-    if (lane == 0) npart[warp] = sq;
+    for (int i = lane; i < n - 1; i += 32) sq = fmaf(P0[i].z, P0[i].z, sq);
+    const float4 r = tri_reflector(warp_sum(sq), P0[0].z, n - 1);
+    if (lane == 0) *scal = r;
   }
   __syncthreads();
   for (int s = 0; s + 1 < n; ++s) {
@@ -298,18 +310,11 @@ static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, u
       __syncthreads();
       return;
     }
-    // reflector s: v = (x - alpha e_1) / ||x - alpha e_1||, alpha = -sign(x_0) ||x||
-    const float ss = tri_sum_parts(npart, nw);
-    const float x0 = Pc[0].z;
-    float alpha = x0, scale = 0.f;  // a length-1 (or zero) column needs no reflection
-    if (m > 1 && ss > 0.f) {
-      const float nx = sqrtf(ss);
-      alpha = (x0 >= 0.f) ? -nx : nx;
-      scale = 1.f / sqrtf(2.f * (ss - x0 * alpha));
-    }
-    const float xh0 = x0 - alpha;
+    // reflector s: v = (x - alpha e_1) * scale, from the scalars warp 0 wrote
+    const float4 sc = *scal;
+    const float alpha = sc.x, scale = sc.y, xh0 = sc.z;
     if (tid == 0) e[s] = alpha;
-    if (m > 1) {
+    {
       float* vpk = A + tri_voff(n, s);  // inside rows 0..s, which are finished
       for (int i = tid; i < m; i += nt) vpk[i] = ((i == 0) ? xh0 : Pc[i].z) * scale;
     }
@@ -336,16 +341,17 @@ static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, u
       if (lane == 0) kpart[warp] = kp;
     }
     __syncthreads();
-    if (m == 1) break;
-    // q_s = 2 (p - K v), and column s+1 updated by step s: its diagonal is
-    // d[s+1], the rest is x_{s+1}; (v_s, q_s, x_{s+1}) go to Pn shifted by one
-    {
+    // warp 0: q_s = 2 (p - K v), column s+1 updated by step s (its diagonal is
+    // d[s+1], the rest is x_{s+1}; (v_s, q_s, x_{s+1}) go to Pn shifted by
+    // one), and the scalars of reflector s+1. One warp does it so that the
+    // norm needs no block-wide reduction and the scalars are computed once.
+    if (warp == 0) {
       const float K = tri_sum_parts(kpart, nw);
       const float v0 = xh0 * scale;
-      const float p0 = tri_group_sum(pp, m, 0, G);
-      const float q0 = 2.f * fmaf(-K, v0, p0);
-      float sq = 0.f;
-      for (int i = tid; i < m; i += nt) {
+      const float q0 = 2.f * fmaf(-K, v0, tri_group_sum(pp, m, 0, G));
+      float sq = 0.f, x1 = 0.f;
+#pragma unroll 4
+      for (int i = lane; i < m; i += 32) {
         const float pi = tri_group_sum(pp, m, i, G);
         const float vi = (i == 0) ? v0 : Pc[i].z * scale;
         const float qi = 2.f * fmaf(-K, vi, pi);
@@ -356,10 +362,13 @@ static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, u
         } else {
           Pn[i - 1] = make_float4(vi, qi, a, 0.f);
           sq = fmaf(a, a, sq);
+          if (i == 1) x1 = a;
         }
       }
-      sq = warp_sum(sq);
-      if (lane == 0) npart[warp] = sq;
+      const float ss = warp_sum(sq);
+      x1 = __shfl_sync(0xffffffffu, x1, 1);  // m > 32: lane 1 holds i = 1
+      const float4 r = tri_reflector(ss, x1, m - 1);
+      if (lane == 0) *scal = r;
     }
     __syncthreads();
   }
