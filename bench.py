@@ -371,6 +371,46 @@ def run_batch(args, w):
                "d2h_bytes_per_step": int(hout.numel() * 4)}
         del host
 
+    # the plain FP32 single-sketch path (K7) against the batched kernel on the
+    # same sample: the first P sketches, one fd_create handle each, appended
+    # on 16 CUDA streams (host wall clock around the appends and a sync), and
+    # one FDBatch launch over the same P sketches (CUDA events)
+    plain = None
+    if not args.no_plain and rank == 0 and args.workload == "c3":
+        P = min(64, count)
+        sub_rows = int(sum(specs[i]["n"] for i in range(P)))
+        streams = [torch.cuda.Stream() for _ in range(16)]
+        hs = [fd.FDSketch(ds[i], ells[i], w["variant"], w["alpha"], "fp32", stream=streams[i % 16])
+              for i in range(P)]
+        for rep in range(2):  # the first pass warms up
+            for h in hs:
+                h.reset()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i in range(P):
+                hs[i].append(blocks[i])
+            torch.cuda.synchronize()
+            dt_plain = time.perf_counter() - t0
+        for h in hs:
+            h.close()
+        bs = fd.FDBatch(ds[:P], ells[:P], w["variant"], w["alpha"], w["prec"])
+        prep_s = bs.prepare({i: blocks[i] for i in range(P)})
+        eb0 = torch.cuda.Event(enable_timing=True)
+        eb1 = torch.cuda.Event(enable_timing=True)
+        for rep in range(2):
+            bs.reset()
+            eb0.record(stream)
+            bs.append_prepared(prep_s)
+            eb1.record(stream)
+            torch.cuda.synchronize()
+        dt_batch = eb0.elapsed_time(eb1) / 1e3
+        bs.close()
+        plain = {"value": sub_rows / dt_plain, "unit": "rows/s",
+                 "batched_same_sample": sub_rows / dt_batch,
+                 "sample": f"first {P} sketches ({sub_rows} rows)",
+                 "how": "one fd_create FP32 handle per sketch on 16 CUDA streams, host wall clock; "
+                        "batched: one persistent launch over the same sketches, CUDA events"}
+
     if rank != 0:
         b.close()
         return 0
@@ -409,6 +449,7 @@ def run_batch(args, w):
                    "input_bytes": int(flat.numel() * flat.element_size()),
                    "l2": "input larger than L2 (no flush needed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "plain_fp32": plain,
         "roofline": roofline, "gpu_launches": 2 * args.steps, "clocks": clk, "e2e": e2e,
         "cpu_baseline": cpu,
     }

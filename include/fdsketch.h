@@ -222,8 +222,16 @@ int fd_cov_err_noalloc(const void* A, int64_t n, int64_t d, int64_t lda, int32_t
 /* Counters of the handle (synchronises the stream). */
 int fd_stats(fd_handle h, fd_stats_t* s);
 
-/* Spectrum of the latest reduction run by fd_append: sigma^2 (descending,
- * 2*ell values) and sigma'^2 aligned with it, FP64, host arrays of 2*ell. */
+/* Record the spectrum of every reduction fd_append runs from now on (on != 0)
+ * or stop (on = 0; the default). While recording, the eigensolve computes
+ * every eigenvalue; otherwise the variants other than SS compute only the
+ * ell+1 largest, the only ones their ReduceRank rule keeps. */
+int fd_record_spectrum(fd_handle h, int32_t on);
+
+/* Spectrum of the latest reduction run by fd_append while recording:
+ * sigma^2 (descending, one value per buffer row: 2*ell, or the buffer_rows
+ * of fd_create_buffered) and sigma'^2 aligned with it, FP64, host arrays of
+ * that length. FD_EINVAL when not recording. */
 int fd_last_spectrum(fd_handle h, double* sigma2, double* sigma_prime2);
 
 /* Return the handle to its just-created state (empty buffer, zero counters)

@@ -79,6 +79,7 @@ struct fd_state {
   int ldp = 0;
   int ksplit = 1;
   int keep = 0;  // rows a reduction leaves in the buffer
+  bool record_spectrum = false;  // fd_record_spectrum
   void* work = nullptr;   // eigensolve matrix in global memory when it does not fit smem
   size_t work_bytes = 0;
   void* wrot = nullptr;   // rotate matrix (ell-1) x ldr
@@ -307,8 +308,8 @@ static int reduce_rows(fd_state* h, int nrows, void* out, int64_t ldo, DevCounte
   a.ldw_work = nrows + (nrows & 1);
   a.ctr_in = h->ctr;
   a.ctr_out = ctr_out;
-  a.sig2_out = diag ? h->sig2 : nullptr;
-  a.sigp2_out = diag ? h->sigp2 : nullptr;
+  a.sig2_out = (diag && h->record_spectrum) ? h->sig2 : nullptr;
+  a.sigp2_out = (diag && h->record_spectrum) ? h->sigp2 : nullptr;
   a.wrot = h->wrot;
   a.ldr = h->ldr;
   a.max_sweeps = h->max_sweeps;
@@ -547,8 +548,14 @@ extern "C" int fd_stats(fd_handle h, fd_stats_t* s) {
   return FD_OK;
 }
 
+extern "C" int fd_record_spectrum(fd_handle h, int32_t on) {
+  if (!h) return FD_EINVAL;
+  h->record_spectrum = (on != 0);
+  return FD_OK;
+}
+
 extern "C" int fd_last_spectrum(fd_handle h, double* sigma2, double* sigma_prime2) {
-  if (!h || !sigma2 || !sigma_prime2) return FD_EINVAL;
+  if (!h || !sigma2 || !sigma_prime2 || !h->record_spectrum) return FD_EINVAL;
   FD_CK(cudaMemcpyAsync(sigma2, h->sig2, (size_t)h->L * 8, cudaMemcpyDeviceToHost, h->st));
   FD_CK(cudaMemcpyAsync(sigma_prime2, h->sigp2, (size_t)h->L * 8, cudaMemcpyDeviceToHost, h->st));
   FD_CK(cudaStreamSynchronize(h->st));

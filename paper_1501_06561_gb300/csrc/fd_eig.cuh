@@ -187,8 +187,11 @@ static __device__ void shrink_sorted(const EigArgs& a, int n, int np, double eps
 }
 
 // FP64 bookkeeping of one reduction (thread 0) and the spectrum diagnostics.
+// total_mass >= 0: sum of all sigma^2 (the trace of G) when mu holds only the
+// leading values; otherwise the sum of mu.
 static __device__ void write_counters(const EigArgs& a, int n, const double* mu, const double* mup,
-                               int count, double dsum, double dlast, int capped, int sweeps) {
+                               int count, double dsum, double dlast, int capped, int sweeps,
+                               double total_mass = -1.0) {
   const int tid = threadIdx.x;
   const int nout = a.ell - 1;
   if (a.sig2_out) for (int k = tid; k < n; k += blockDim.x) { a.sig2_out[k] = mu[k]; a.sigp2_out[k] = mup[k]; }
@@ -196,6 +199,7 @@ static __device__ void write_counters(const EigArgs& a, int n, const double* mu,
     DevCounters c = *a.ctr_in;
     double rem = 0.0, nb = 0.0;
     for (int k = 0; k < n; ++k) { rem += mu[k] - mup[k]; nb += mup[k]; }
+    if (total_mass >= 0.0) rem = total_mass - nb;
     c.sum_delta += dsum;
     c.last_delta = dlast;
     c.removed += rem;

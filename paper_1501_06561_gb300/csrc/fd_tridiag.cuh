@@ -405,11 +405,12 @@ __device__ __forceinline__ int tri_sturm(const float* d, const float* e2, int n,
 }
 
 // ---------------------------------------------------------------------------
-// Step 2. lam[j] = j-th largest eigenvalue of T. cnt: blockDim.x ints of
-// scratch. Returns the Gershgorin bound of ||T|| through *tnorm_out (shared).
+// Step 2. lam[j] = j-th largest eigenvalue of T for j < nl (0 for the rest).
+// cnt: blockDim.x ints of scratch. Returns the Gershgorin bound of ||T||
+// through *tnorm_out (shared).
 // ---------------------------------------------------------------------------
 static __device__ void tri_bisect(const float* d, const float* e, float* e2, int n, float* lam,
-                                  float* tnorm_out, int* cnt) {
+                                  float* tnorm_out, int* cnt, int nl) {
   const int tid = threadIdx.x, nt = blockDim.x;
   __shared__ float s_lo, s_hi;
   for (int i = tid; i < n - 1; i += nt) e2[i] = e[i] * e[i];
@@ -437,12 +438,13 @@ static __device__ void tri_bisect(const float* d, const float* e, float* e2, int
   cnt[tid] = tri_sturm(d, e2, n, lo0 + (float)(tid + 1) * h, pivmin);
   __syncthreads();
   int G = 1;  // lanes per eigenvalue (power of two, <= 8)
-  while (G < 8 && 2 * G * n <= nt) G <<= 1;
+  while (G < 8 && 2 * G * nl <= nt) G <<= 1;
   const int sub = tid & (G - 1);
   const int per = nt / G;
-  for (int j0 = 0; j0 < n; j0 += per) {
+  for (int j = nl + tid; j < n; j += nt) lam[j] = 0.f;  // not needed by the caller
+  for (int j0 = 0; j0 < nl; j0 += per) {
     const int j = j0 + tid / G;
-    const bool act = j < n;
+    const bool act = j < nl;
     const int target = n - 1 - j;  // lambda_j is the target-th smallest (0-based)
     float lo = lo0, hi = hi0;
     if (act) {
@@ -777,108 +779,88 @@ __device__ bool tri_cholqr(float* Zt, int ldz, int n, int count, float* C, int l
 // ---------------------------------------------------------------------------
 // Fallback of steps 3-4: inverse iteration from a random start for vectors
 // list[c0 .. min(c0+NB, cend)-1] (c0 + t itself without a list; thread
-// t < NB takes one): eigenvalue lam[pos[c]], (T - lambda I) z = z solved
-// `reps` times by LU with partial pivoting. scr holds NB interleaved copies of the four LU bands, piv NB x n
-// pivot flags.
+// t < NB takes one): eigenvalue lam[pos[c]], (T - lambda I) z = z0 solved
+// once by LU with partial pivoting, z0 eliminated during the factorisation.
+// Divisions use the fast reciprocal: the solve only has to amplify the
+// eigenvector direction. scr holds NB interleaved copies of the three bands
+// of U (1/U_ii stored).
 // ---------------------------------------------------------------------------
 template <int NB>
 __device__ void tri_invit_batch(float* Zt, int ldz, int n, const float* d, const float* e,
                                 const float* lam, const int* pos, const int* list, int c0,
-                                int cend, float tnorm, float* scr, unsigned char* piv, int reps) {
+                                int cend, float tnorm, float* scr) {
   const int t = threadIdx.x;
   if (t >= NB || c0 + t >= cend) return;
   const int c = list ? list[c0 + t] : c0 + t;
-  float* dd = scr;
-  float* du = scr + (size_t)NB * n;
-  float* du2 = scr + (size_t)2 * NB * n;
-  float* dl = scr + (size_t)3 * NB * n;
+  float* ru = scr;                      // 1 / U_ii
+  float* du = scr + (size_t)NB * n;     // U_{i,i+1}
+  float* du2 = scr + (size_t)2 * NB * n;  // U_{i,i+2} (fill from row swaps)
   float* z = Zt + c;
-#define DD(i) dd[(size_t)(i) * NB + t]
+#define RU(i) ru[(size_t)(i) * NB + t]
 #define DU(i) du[(size_t)(i) * NB + t]
 #define DU2(i) du2[(size_t)(i) * NB + t]
-#define DL(i) dl[(size_t)(i) * NB + t]
-#define PV(i) piv[(size_t)(i) * NB + t]
 #define Z(i) z[(size_t)(i) * ldz]
   const float eps = 1.1920929e-07f;
   const float tiny = eps * fmaxf(tnorm, 1e-30f);
   const float lmb = lam[pos[c]];
-  for (int i = 0; i < n; ++i) {
-    DD(i) = d[i] - lmb;
-    if (i < n - 1) {
-      DU(i) = e[i];
-      DL(i) = e[i];
-      DU2(i) = 0.f;
-    }
-  }
-  for (int i = 0; i + 1 < n; ++i) {
-    const float di = DD(i), li = DL(i);
-    if (fabsf(di) >= fabsf(li)) {
-      const float dv = (di == 0.f) ? tiny : di;
-      DD(i) = dv;
-      const float f = li / dv;
-      DL(i) = f;
-      DD(i + 1) = DD(i + 1) - f * DU(i);
-      PV(i) = 0;
-    } else {
-      const float f = di / li;
-      DD(i) = li;
-      DL(i) = f;
-      const float tmp = DU(i);
-      const float dn = DD(i + 1);
-      DU(i) = dn;
-      DD(i + 1) = tmp - f * dn;
-      if (i + 2 < n) {
-        DU2(i) = DU(i + 1);
-        DU(i + 1) = -f * DU(i + 1);
-      }
-      PV(i) = 1;
-    }
-  }
-  if (DD(n - 1) == 0.f) DD(n - 1) = tiny;
-  for (int i = 0; i < n; ++i) {  // start: ones with a small deterministic perturbation
+  // start vector: ones with a small deterministic perturbation (a hash of i, c)
+  auto start = [c](int i) {
     unsigned h = (unsigned)(i * 2654435761u) ^ (unsigned)(c * 40503u + 0x9e3779b9u);
     h ^= h >> 15;
     h *= 2246822519u;
     h ^= h >> 13;
-    Z(i) = 1.f + 0.25f * ((float)(h & 0xffff) / 65536.f - 0.5f);
+    return 1.f + 0.25f * ((float)(h & 0xffff) / 65536.f - 0.5f);
+  };
+  // LU with partial pivoting of T - lmb I, the start vector eliminated along:
+  // (dc, uc, u2c | zc) is the current row restricted to columns i, i+1, i+2
+  float dc = d[0] - lmb, uc = (n > 1) ? e[0] : 0.f, u2c = 0.f, zc = start(0);
+  for (int i = 0; i + 1 < n; ++i) {
+    const float li = e[i];  // row i+1, column i
+    const float dn = d[i + 1] - lmb, un = (i + 2 < n) ? e[i + 1] : 0.f, zn = start(i + 1);
+    if (fabsf(dc) >= fabsf(li)) {
+      const float dv = (dc == 0.f) ? tiny : dc;
+      const float f = __fdividef(li, dv);
+      RU(i) = __fdividef(1.f, dv);
+      DU(i) = uc;
+      DU2(i) = u2c;
+      Z(i) = zc;
+      dc = fmaf(-f, uc, dn);
+      uc = fmaf(-f, u2c, un);
+      zc = fmaf(-f, zc, zn);
+    } else {  // row i+1 becomes the pivot row
+      const float f = __fdividef(dc, li);
+      RU(i) = __fdividef(1.f, li);
+      DU(i) = dn;
+      DU2(i) = un;
+      Z(i) = zn;
+      dc = fmaf(-f, dn, uc);
+      uc = fmaf(-f, un, u2c);
+      zc = fmaf(-f, zn, zc);
+    }
+    u2c = 0.f;
   }
-  for (int rep = 0; rep < reps; ++rep) {
-    for (int i = 0; i + 1 < n; ++i) {
-      if (!PV(i)) {
-        Z(i + 1) = Z(i + 1) - DL(i) * Z(i);
-      } else {
-        const float tmp = Z(i);
-        Z(i) = Z(i + 1);
-        Z(i + 1) = tmp - DL(i) * Z(i);
-      }
-    }
-    float x2 = 0.f, x1 = 0.f;  // z[i+2], z[i+1]
-    for (int i = n - 1; i >= 0; --i) {
-      float v = Z(i);
-      if (i + 1 < n) v -= DU(i) * x1;
-      if (i + 2 < n) v -= DU2(i) * x2;
-      v /= DD(i);
-      Z(i) = v;
-      x2 = x1;
-      x1 = v;
-    }
-    float mx = 0.f;
-    for (int i = 0; i < n; ++i) mx = fmaxf(mx, fabsf(Z(i)));
-    const float inv = (mx > 0.f) ? 1.f / mx : 1.f;
-    float s2 = 0.f;
-    for (int i = 0; i < n; ++i) {
-      const float v = Z(i) * inv;
-      Z(i) = v;
-      s2 = fmaf(v, v, s2);
-    }
-    const float r = rsqrtf(fmaxf(s2, 1e-30f));
-    for (int i = 0; i < n; ++i) Z(i) *= r;
+  // back substitution, tracking the largest entry
+  float x = zc * __fdividef(1.f, (dc == 0.f) ? tiny : dc), x2 = 0.f, mx = fabsf(x);
+  Z(n - 1) = x;
+  for (int i = n - 2; i >= 0; --i) {
+    const float v = fmaf(-DU2(i), x2, fmaf(-DU(i), x, Z(i))) * RU(i);
+    Z(i) = v;
+    x2 = x;
+    x = v;
+    mx = fmaxf(mx, fabsf(v));
   }
-#undef DD
+  const float inv = (mx > 0.f) ? 1.f / mx : 1.f;
+  float s2 = 0.f;
+  for (int i = 0; i < n; ++i) {
+    const float v = Z(i) * inv;
+    Z(i) = v;
+    s2 = fmaf(v, v, s2);
+  }
+  const float r = rsqrtf(fmaxf(s2, 1e-30f));
+  for (int i = 0; i < n; ++i) Z(i) *= r;
+#undef RU
 #undef DU
 #undef DU2
-#undef DL
-#undef PV
 #undef Z
 }
 
@@ -888,11 +870,16 @@ __device__ void tri_invit_batch(float* Zt, int ldz, int n, const float* d, const
 // through *nlist, shared).
 static __device__ void tri_cluster_members(const float* lam, const int* pos, int n, int count,
                                            float gtol, int* ord, int* list, int* nlist) {
+  // ord: retained vectors by their position in the spectrum (the positions
+  // pos[r] are distinct), one rank per thread
+  for (int r = threadIdx.x; r < count; r += blockDim.x) {
+    const int pr = pos[r];
+    int rank = 0;
+    for (int q = 0; q < count; ++q) rank += (pos[q] < pr);
+    ord[rank] = r;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    int k = 0;
-    for (int q = 0; q < n && k < count; ++q)
-      for (int r = 0; r < count; ++r)
-        if (pos[r] == q) ord[k++] = r;
     int nl = 0;
     for (int a = 0; a < count;) {
       int b = a + 1;
@@ -1265,8 +1252,19 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
   __shared__ int s_count, s_ok;
   __shared__ double s_dsum, s_dlast;
 
+  // Values past the (ell+1)-th are zeroed by every rule but SS, so only SS and
+  // a recorded spectrum need them; without them the removed mass comes from
+  // the trace of G (FP64, taken before step 1 changes the diagonal).
+  const int nl = (a.variant == FD_VAR_SS || a.sig2_out) ? n : min(n, a.ell + 1);
+  __shared__ double s_trace;
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) t += (double)A[(size_t)i * ld + i];
+    t = warp_sum(t);
+    if (threadIdx.x == 0) s_trace = t;
+  }
   tri_reduce(A, ld, n, d, e, rw, red);
-  tri_bisect(d, e, e2, n, lam, &s_tnorm, reinterpret_cast<int*>(scr_raw));
+  tri_bisect(d, e, e2, n, lam, &s_tnorm, reinterpret_cast<int*>(scr_raw), nl);
   {
     // eigenvalues at or below the bisection's resolution (2 eps lambda_1)
     // are zero: their sign and size are rounding noise
@@ -1308,14 +1306,13 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
     __shared__ int s_nl;
     __syncthreads();
     float* scr = reinterpret_cast<float*>(scr_raw);
-    unsigned char* piv = scr_raw + tri_al16((size_t)NB * n * 16);
     int* ord = reinterpret_cast<int*>(pb);
     int* list = ord + count;
     bool redo = s_ok == 0;
     if (!redo) {
       tri_cluster_members(lam, pos, n, count, 1e-4f * tnorm, ord, list, &s_nl);
       for (int c0 = 0; c0 < s_nl; c0 += NB) {
-        tri_invit_batch<NB>(Zt, ldz, n, d, e, lam, pos, list, c0, s_nl, tnorm, scr, piv, 1);
+        tri_invit_batch<NB>(Zt, ldz, n, d, e, lam, pos, list, c0, s_nl, tnorm, scr);
         __syncthreads();
       }
       const int ldc = tri_ldz(count);
@@ -1326,14 +1323,14 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
     if (redo) {
       __syncthreads();
       for (int c0 = 0; c0 < count; c0 += NB) {
-        tri_invit_batch<NB>(Zt, ldz, n, d, e, lam, pos, nullptr, c0, count, tnorm, scr, piv, 1);
+        tri_invit_batch<NB>(Zt, ldz, n, d, e, lam, pos, nullptr, c0, count, tnorm, scr);
         __syncthreads();
       }
       tri_cgs2(Zt, ldz, n, count, xb, red);
     }
   }
   tri_back_write<R, MAXJ, VPT>(a, A, n, Zt, ldz, count, mu, mup, pos, vb0);  // vb0..pb: 4 np8 floats
-  write_counters(a, n, mu, mup, s_count, s_dsum, s_dlast, 0, 1);
+  write_counters(a, n, mu, mup, s_count, s_dsum, s_dlast, 0, 1, nl < n ? s_trace * smax : -1.0);
 }
 
 }  // namespace fdk

@@ -64,6 +64,7 @@ def load():
         "fd_create_buffered": [i64, i32, i32, dbl, i32, i32, vp, ctypes.POINTER(vp)],
         "fd_append": [vp, vp, i64, i64, i32, i32],
         "fd_sketch": [vp, vp, i32, i32],
+        "fd_record_spectrum": [vp, i32],
         "fd_sketch_compensated": [vp, vp, i32, i32],
         "fd_merge": [vp, vp],
         "fd_cov_err": [vp, vp, i64, i64, i32, i32, ctypes.POINTER(dbl)],
@@ -162,6 +163,7 @@ class FDSketch:
                  prec: str = "fp32", stream=None, buffer_rows: int | None = None):
         lib = load()
         self.d, self.ell, self.variant, self.prec = d, ell, variant, prec
+        self.buffer_rows = buffer_rows or (ell if variant == "fastpfd" else 2 * ell)
         self._stream = _stream_ptr(stream)
         h = ctypes.c_void_p()
         if buffer_rows is None:
@@ -229,8 +231,12 @@ class FDSketch:
         _check(load().fd_stats(self._h, ctypes.byref(s)), "fd_stats")
         return {f: getattr(s, f) for f, _ in Stats._fields_}
 
+    def record_spectrum(self, on: bool = True):
+        """Keep the spectrum of each reduction for last_spectrum() (fd_record_spectrum)."""
+        _check(load().fd_record_spectrum(self._h, 1 if on else 0), "fd_record_spectrum")
+
     def last_spectrum(self):
-        L = 2 * self.ell
+        L = self.buffer_rows
         a = np.zeros(L)
         b = np.zeros(L)
         _check(load().fd_last_spectrum(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),

@@ -59,6 +59,8 @@ def test_parity_small_ragged(prec, variant):
     ce_g, ce_o = cov_err(A, B), cov_err(A, Bo)
     assert abs(ce_g - ce_o) <= COV_ABS, (ce_g, ce_o)
     assert abs(st["sketch_sum_delta"] - io["sum_delta"]) <= 1e-4 * io["sum_delta"]
+    # removed mass (from the trace of G when only the leading values are solved)
+    assert abs(st["sketch_removed"] - io["removed"]) <= 1e-4 * io["removed"]
     assert st["noconv"] == 0
 
 
@@ -97,6 +99,9 @@ def test_single_reduction_spectrum(prec, variant):
     ell = 37
     A = W.random_noisy(2 * ell, 411, m=20, seed=23, dtype=np.float32)
     with fd.FDSketch(411, ell, variant, _alpha(variant), prec) as s:
+        with pytest.raises(fd.FDError):
+            s.last_spectrum()  # not recording
+        s.record_spectrum()
         s.append(torch.from_numpy(A).cuda())
         sig2, sigp2 = s.last_spectrum()
         B = s.sketch()
