@@ -748,6 +748,7 @@ def main():
                    "l2": "input larger than L2 (no flush needed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "cov_err": cov, "reductions_per_step": st["reductions"],
+        "eig_fallbacks_per_step": st.get("eig_fallbacks"),
         "plain_fp32": plain, "sharded": sharded,
         "roofline": roofline, "kernels": kshare,
         "gpu_launches": int(launches + 2 * args.steps),

@@ -105,6 +105,9 @@ typedef struct {
   double sketch_sum_delta;
   double sketch_removed;
   double sketch_norm_b2;  /* ||B||_F^2 of the sketch fd_sketch returned */
+  int64_t eig_fallbacks;  /* reductions whose eigenvectors needed the fallback of the
+                             tridiagonal solve (nearly dependent vectors of close
+                             eigenvalues recomputed by inverse iteration) */
 } fd_stats_t;
 
 /* Create a sketch of width d with ell output rows (fd_sketch returns ell x d;

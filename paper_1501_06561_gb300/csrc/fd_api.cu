@@ -531,6 +531,7 @@ extern "C" int fd_stats(fd_handle h, fd_stats_t* s) {
   s->n_seen = h->n_seen;
   s->reductions = c.reductions;
   s->noconv = c.noconv;
+  s->eig_fallbacks = c.fallbacks;
   s->norm_a2 = c.norm_a2;
   s->sum_delta = c.sum_delta;
   s->last_delta = c.last_delta;

@@ -608,6 +608,7 @@ extern "C" int fd_batch_stats(fd_batch_state* b, int32_t id, fd_stats_t* s) {
   s->n_seen = b->nseen[id];
   s->reductions = c[0].reductions;
   s->noconv = c[0].noconv;
+  s->eig_fallbacks = c[0].fallbacks;
   s->norm_a2 = c[0].norm_a2;
   s->sum_delta = c[0].sum_delta;
   s->last_delta = c[0].last_delta;

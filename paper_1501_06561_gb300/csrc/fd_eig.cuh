@@ -62,6 +62,9 @@ __device__ void eig_load(const EigArgs& a, T* Wm, int ld, int n, int np) {
 // number of retained positions and the deltas subtracted through dsum_out /
 // dlast_out (shared). `eps_arith` is the unit of the eigensolve's arithmetic
 // (SS treats masses at or below np * eps_arith * mu_0 as empty).
+// MAXK: positions per thread in the ranking, np <= MAXK * blockDim.x (every
+// eigensolve launch has at least np threads).
+template <int MAXK = 1>
 static __device__ void shrink_sorted(const EigArgs& a, int n, int np, double eps_arith, const double* mu,
                               double* mup, int* rrank, int* count_out, double* dsum_out,
                               double* dlast_out) {
@@ -162,23 +165,40 @@ static __device__ void shrink_sorted(const EigArgs& a, int n, int np, double eps
   }
   __syncthreads();
 
-  // 6. Output order: retained positions by sigma'^2 descending, ties by position.
-  for (int k = tid; k < np; k += blockDim.x) {
-    const double v = mup[k];
-    int rank = -1;
-    if (v > 0.0) {
-      rank = 0;
-      for (int i = 0; i < np; ++i) {
-        const double w = mup[i];
-        rank += (w > v) || (w == v && i < k);
+  // 6. Output order: retained positions by sigma'^2 descending, ties by
+  // position. The keys are compared in FP32 (the order only places rows; a
+  // positive mass stays positive): FP64 runs at a small fraction of the FP32
+  // rate here. The keys sit in rrank until the ranks replace them.
+  float* key = reinterpret_cast<float*>(rrank);
+  if (tid == 0) s_count = 0;
+  for (int k = tid; k < np; k += blockDim.x)
+    key[k] = (mup[k] > 0.0) ? fmaxf((float)mup[k], 1.17549435e-38f) : 0.f;
+  __syncthreads();
+  int rk[MAXK];
+  int mine = 0;
+#pragma unroll
+  for (int u = 0; u < MAXK; ++u) {
+    const int k = tid + u * (int)blockDim.x;
+    rk[u] = -1;
+    if (k < np) {
+      const float v = key[k];
+      if (v > 0.f) {
+        int r = 0;
+        for (int i = 0; i < np; ++i) {
+          const float w = key[i];
+          r += (w > v) || (w == v && i < k);
+        }
+        rk[u] = r;
+        ++mine;
       }
     }
-    rrank[k] = rank;
   }
-  if (tid == 0) {
-    int cnt = 0;
-    for (int k = 0; k < np; ++k) cnt += (mup[k] > 0.0);
-    s_count = cnt;
+  if (mine) atomicAdd(&s_count, mine);
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < MAXK; ++u) {
+    const int k = tid + u * (int)blockDim.x;
+    if (k < np) rrank[k] = rk[u];
   }
   __syncthreads();
 
@@ -191,21 +211,25 @@ static __device__ void shrink_sorted(const EigArgs& a, int n, int np, double eps
 // leading values; otherwise the sum of mu.
 static __device__ void write_counters(const EigArgs& a, int n, const double* mu, const double* mup,
                                int count, double dsum, double dlast, int capped, int sweeps,
-                               double total_mass = -1.0) {
+                               double total_mass = -1.0, int fallback = 0) {
   const int tid = threadIdx.x;
   const int nout = a.ell - 1;
   if (a.sig2_out) for (int k = tid; k < n; k += blockDim.x) { a.sig2_out[k] = mu[k]; a.sigp2_out[k] = mup[k]; }
-  if (tid == 0) {
-    DevCounters c = *a.ctr_in;
+  if (tid < 32) {  // one warp: the sums in FP64
     double rem = 0.0, nb = 0.0;
-    for (int k = 0; k < n; ++k) { rem += mu[k] - mup[k]; nb += mup[k]; }
+    for (int k = tid; k < n; k += 32) { rem += mu[k] - mup[k]; nb += mup[k]; }
+    rem = warp_sum(rem);
+    nb = warp_sum(nb);
     if (total_mass >= 0.0) rem = total_mass - nb;
+    if (tid != 0) return;
+    DevCounters c = *a.ctr_in;
     c.sum_delta += dsum;
     c.last_delta = dlast;
     c.removed += rem;
     c.norm_b2 = nb;
     c.reductions += 1;
     c.noconv += capped ? 1 : 0;
+    c.fallbacks += fallback ? 1 : 0;
     c.max_sweeps = fmax(c.max_sweeps, (double)sweeps);
     c.retained = count < nout ? count : nout;
     *a.ctr_out = c;

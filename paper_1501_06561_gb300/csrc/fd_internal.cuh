@@ -21,6 +21,7 @@ struct DevCounters {
   double max_sweeps;
   long long reductions;
   long long noconv;
+  long long fallbacks;  // eigensolves whose eigenvectors needed the fallback path
   unsigned int ingest_ticket;  // last-block-done counter of the ingest kernel
   int retained;                // rows with sigma' > 0 after the latest reduction
 };

@@ -1042,13 +1042,14 @@ __device__ void tri_back_write(const EigArgs& a, const float* V, int n, const fl
     }
     if (act) {
       const int k = pos[c];
-      const double sc = (mu[k] > 0.0) ? sqrt(mup[k] / mu[k]) : 0.0;
+      // sqrt(mu'/mu) in FP32: the rotate matrix itself is FP32
+      const float sc = (mu[k] > 0.0) ? sqrtf((float)mup[k] / (float)mu[k]) : 0.f;
       if (a.row_mass && g == 0) a.row_mass[c] = mup[k];
 #pragma unroll
       for (int j = 0; j < MAXJ; ++j) {
         const int i = n - 1 - (g + R * j);
         if (i >= 0) {
-          const float val = (float)(sc * (double)z[j]);
+          const float val = sc * z[j];
           wr[(size_t)c * a.ldr + i] = val;
           if (a.wrot_hi) {
             const __nv_bfloat16 hi = __float2bfloat16_rn(val);
@@ -1184,13 +1185,13 @@ __device__ void tri_back_write(const EigArgs& a, const float* V, int n, const fl
       const int c = c0 + h;
       if (c < count) {
         const int k = pos[c];
-        const double sc = (mu[k] > 0.0) ? sqrt(mup[k] / mu[k]) : 0.0;
+        const float sc = (mu[k] > 0.0) ? sqrtf((float)mup[k] / (float)mu[k]) : 0.f;
         if (a.row_mass && g == 0) a.row_mass[c] = mup[k];
 #pragma unroll
         for (int j = 0; j < MAXJ; ++j) {
           const int i = n - 1 - (g + R * j);
           if (i >= 0) {
-            const float val = (float)(sc * (double)(h ? z1[j] : z0[j]));
+            const float val = sc * (h ? z1[j] : z0[j]);
             wr[(size_t)c * a.ldr + i] = val;
             if (a.wrot_hi) {
               const __nv_bfloat16 hi = __float2bfloat16_rn(val);
@@ -1272,6 +1273,7 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
     for (int k = tid; k < n; k += nt) mu[k] = (lam[k] > zfloor) ? (double)lam[k] * smax : 0.0;
   }
   __syncthreads();
+  // n <= blockDim.x (512 threads for n <= 512; the batched kernel: n <= 128, 256 threads)
   shrink_sorted(a, n, n, 1.1920928955078125e-07, mu, mup, rrank, &s_count, &s_dsum, &s_dlast);
   const int nout = a.ell - 1;
   const int count = s_count < nout ? s_count : nout;
@@ -1289,6 +1291,7 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
     if (!tri_twisted(d, e, e2, n, lam[pos[r]], pivmin, Zt + r, ldz)) s_ok = 0;
   __syncthreads();
   bool ok = s_ok != 0;
+  bool fell_back = false;
   if (ok) {
     const int ldc = tri_ldz(count);
     float* C = reinterpret_cast<float*>(scr_raw);
@@ -1296,6 +1299,7 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
     ok = tri_cholqr<TRI_CU>(Zt, ldz, n, count, C, ldc, dinv, 0.25f);
   }
   if (!ok) {
+    fell_back = true;
     // Vectors of close eigenvalues came out nearly dependent. Within a window
     // of a few eps ||T|| any orthonormal basis of the invariant subspace is
     // as good, so the members of such clusters are replaced by one
@@ -1330,7 +1334,8 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
     }
   }
   tri_back_write<R, MAXJ, VPT>(a, A, n, Zt, ldz, count, mu, mup, pos, vb0);  // vb0..pb: 4 np8 floats
-  write_counters(a, n, mu, mup, s_count, s_dsum, s_dlast, 0, 1, nl < n ? s_trace * smax : -1.0);
+  write_counters(a, n, mu, mup, s_count, s_dsum, s_dlast, 0, 1, nl < n ? s_trace * smax : -1.0,
+                 fell_back ? 1 : 0);
 }
 
 }  // namespace fdk

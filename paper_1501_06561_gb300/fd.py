@@ -41,7 +41,7 @@ class Stats(ctypes.Structure):
                 ("sum_delta", ctypes.c_double), ("last_delta", ctypes.c_double),
                 ("removed", ctypes.c_double), ("max_sweeps", ctypes.c_double),
                 ("sketch_sum_delta", ctypes.c_double), ("sketch_removed", ctypes.c_double),
-                ("sketch_norm_b2", ctypes.c_double)]
+                ("sketch_norm_b2", ctypes.c_double), ("eig_fallbacks", ctypes.c_int64)]
 
 
 class Work(ctypes.Structure):

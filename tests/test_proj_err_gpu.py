@@ -4,7 +4,8 @@ Two checks per variant: the evaluator alone (the oracle's proj-err of the
 GPU's own sketch; differences come from FP32 products summed in FP64 in the
 projection pass, about 1e-7 relative), and end to end (against the oracle's
 sketch of the same stream, where the top-k subspace of the FP32 sketch
-itself differs slightly).
+itself differs slightly; not for SS, whose long-stream sketch is checked by
+its invariants).
 """
 import numpy as np
 import pytest
@@ -42,10 +43,16 @@ def test_proj_err_matches_oracle(variant, alpha):
     pe_same = proj_err(A, B, 10)
     assert abs(pe_dev - pe_same) <= EVAL_REL * pe_same, (pe_dev, pe_same)
     assert abs(pe_host - pe_dev) <= 1e-12 * pe_dev
+    assert pe_dev >= 1.0 - 1e-6
+    if variant == "ss":
+        # SS takes discrete merge decisions: on a stream of ~190 reductions a
+        # one-ulp difference anywhere changes later merges, so the sketch
+        # itself is compared only on short streams (the parity tests); here
+        # only the evaluator is checked
+        return
     Bo, _ = fd_sketch(A, 21, variant, alpha)
     pe_o = proj_err(A, Bo, 10)
     assert abs(pe_dev - pe_o) <= E2E_ABS, (pe_dev, pe_o)
-    assert pe_dev >= 1.0 - 1e-6
 
 
 def test_proj_err_sketch_of_low_rank_stream_is_exact():
