@@ -51,9 +51,9 @@ FP32_LANES_PER_SM = 128
 # buffer rows); profiles/eig_gram_rotate_c1_ell100_full.md.
 EIG_TRAFFIC = {(100, "bf16x3", "fd", 200): 474368}
 # Batched: DRAM bytes per byte of input rows, from a 64-sketch launch of the
-# same generator (1,860,355,824 B for 1,817,569,744 B of rows), scaled by the
+# same generator (1,858,720,080 B for 1,817,569,744 B of rows), scaled by the
 # rows a launch reads; profiles/batch_kernel_c3_64sketch_full.md.
-BATCH_TRAFFIC_PER_INPUT_BYTE = 1860355824 / 1817569744
+BATCH_TRAFFIC_PER_INPUT_BYTE = 1858720080 / 1817569744
 
 
 def parse():
