@@ -43,6 +43,9 @@ WORKLOADS = {
                     "n in U{1000..50000}, k = ell/2, bf16 rows"),
 }
 FP32_LANES_PER_SM = 128
+METRIC_SINGLE = "FD rows/s (sketch update, whole stream per step)"
+METRIC_BATCH = "FD rows/s (batched sketch update, every stream per step)"
+METRIC_SERVE = "serving append latency p99 (ms) and rows/s"
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
 # kernel from one full ncu capture, reported as roofline "traffic" only for
@@ -215,19 +218,41 @@ def run_reference_batch(args, w):
     return rows, t, f"{len(pick)} streams of the batch (ids {pick}, {rows} rows) per step"
 
 
+def run_reference_serve(args, w):
+    """Oracle on a sample of the serving workload: a few sketches, each fed
+    sparse non-negative rows drawn as the request blocks are."""
+    from oracle import FDOracle
+    from paper_1501_06561_gb300 import workloads
+    nsk, per = 4, 4096
+    data = [workloads.sparse_nonneg_rows(per, w["d"], seed=w["seed"], stream=k) for k in range(nsk)]
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for a in data:
+            o = FDOracle(w["d"], w["ell"], w["variant"], w["alpha"])
+            o.append(a)
+            o.sketch()
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    return nsk * per, sum(times) / len(times), f"{nsk} sketches x {per} rows per step"
+
+
 def run_reference(args, w):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    if args.workload == "c3":
-        rows, t, sample = run_reference_batch(args, w)
+    if args.workload in ("c3", "c4"):
+        rows, t, sample = (run_reference_batch(args, w) if args.workload == "c3"
+                           else run_reference_serve(args, w))
         try:
             from threadpoolctl import threadpool_info
             cores = max([x.get("num_threads", 1) for x in threadpool_info()] + [1])
         except Exception:
             cores = os.cpu_count() or 1
         val = rows / t
-        print(json.dumps({"impl": "reference", "metric": "FD rows/s", "value": val,
+        print(json.dumps({"impl": "reference",
+                          "metric": METRIC_BATCH if args.workload == "c3" else METRIC_SERVE,
+                          "value": val,
                           "unit": "rows/s", "n_gpus": args.gpus, "steps": args.steps,
                           "warmup": args.warmup, "ms_per_step": t * 1e3,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -257,11 +282,14 @@ def run_reference(args, w):
     except Exception:
         cores = os.cpu_count() or 1
     val = rows / t
-    line = {"impl": "reference", "metric": "FD rows/s", "value": val, "unit": "rows/s",
+    line = {"impl": "reference", "metric": METRIC_SINGLE, "value": val, "unit": "rows/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["name"], "ell": w["ell"], "variant": w["variant"],
+                       "alpha": w["alpha"],
+                       "buffer_rows": w.get("buffer_rows") or (w["ell"] if w["variant"] == "fastpfd"
+                                                               else 2 * w["ell"]),
                        "sample_rows": rows},
             "cpu_baseline": {"kind": "oracle", "cores": int(cores), "value": val, "unit": "rows/s",
                              "sample": f"first {rows} rows of the workload stream per step"},
@@ -438,7 +466,7 @@ def run_batch(args, w):
     if not args.no_cpu_baseline:
         cpu = cpu_baseline_batch(specs, flat, views, w)
     line = {
-        "metric": "FD rows/s (batched sketch update, every stream per step)",
+        "metric": METRIC_BATCH,
         "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (bf16 rows), f64 shrink",
@@ -544,7 +572,7 @@ def run_serve(args, w):
     if rank != 0:
         return 0
     rows_done = c["rows_done"]
-    line = {"metric": "serving append latency p99 (ms) and rows/s", "value": rows_done / (t_drain - t_start),
+    line = {"metric": METRIC_SERVE, "value": rows_done / (t_drain - t_start),
             "unit": "rows/s", "n_gpus": world, "steps": 1, "warmup": 0,
             "ms_per_step": (t_drain - t_start) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32, f64 shrink", "data": "synthetic",
@@ -733,7 +761,7 @@ def main():
     if not args.no_cpu_baseline and rank == 0:
         cpu = cpu_baseline(w, args.cpu_sample_rows or default_sample_rows(w))
     line = {
-        "metric": "FD rows/s (sketch update, whole stream per step)",
+        "metric": METRIC_SINGLE,
         "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
