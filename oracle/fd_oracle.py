@@ -99,7 +99,9 @@ def reduce_rank(sigma, ell: int, variant: str, alpha: float = 1.0,
 
     ``mass_floor`` (SS only): squared values at or below it count as empty
     slots and are freed before any merge, so that SS never moves mass onto a
-    direction the SVD left undetermined (a numerically zero singular value).
+    direction the SVD left undetermined (a numerically zero singular value);
+    their total is added to the smallest retained direction at the end (one
+    more delta), so that SS keeps ``||B||_F^2 = ||A||_F^2``.
     """
     s = np.asarray(sigma, dtype=np.float64)
     L = s.shape[0]
@@ -139,6 +141,7 @@ def reduce_rank(sigma, ell: int, variant: str, alpha: float = 1.0,
     if variant == "ss":
         mu = sq.copy()
         alive = [j for j in range(L) if mu[j] > mass_floor]
+        freed = float(sum(mu[j] for j in range(L) if not mu[j] > mass_floor))
         deltas = []
         while len(alive) > ell - 1:
             # smallest mass first; among equal masses the larger slot index
@@ -150,6 +153,12 @@ def reduce_rank(sigma, ell: int, variant: str, alpha: float = 1.0,
             mu[p] = 0.0
             alive.remove(p)
             deltas.append(delta)
+        if freed > 0.0 and alive:
+            # the freed masses go to the smallest retained direction, so that
+            # SS keeps the mass of the stream
+            q = min(alive, key=lambda j: (mu[j], -j))
+            mu[q] = mu[q] + freed
+            deltas.append(freed)
         sp = np.zeros_like(s)
         for j in range(L):
             if j not in alive:

@@ -104,10 +104,19 @@ static __device__ void shrink_sorted(const EigArgs& a, int n, int np, double eps
     if (tid == 0) { s_dsum = delta; s_dlast = delta; }
   } else if (warp == 0) {
     // SS (Algorithm 3, repeated): masses at or below the numerical-rank floor
-    // are empty; then merge the second-smallest into the smallest until ell-1
-    // directions remain. Ties: the larger sorted position counts as smaller.
+    // are empty and freed first; then merge the second-smallest into the
+    // smallest until ell-1 directions remain. Ties: the larger sorted position
+    // counts as smaller.
+    // Their total is added to the smallest retained direction at the end, so
+    // the sketch keeps the mass of the stream (SS conserves ||B||_F^2).
     const double flo = mu[0] * (double)np * eps_arith;
-    for (int k = lane; k < np; k += 32) mup[k] = (k < n && mu[k] > flo) ? mu[k] : 0.0;
+    double freed = 0.0;
+    for (int k = lane; k < np; k += 32) {
+      const double v = (k < n) ? mu[k] : 0.0;
+      mup[k] = (v > flo) ? v : 0.0;
+      if (!(v > flo)) freed += v;
+    }
+    freed = warp_sum(freed);
     __syncwarp();
     int alive = 0;
     for (int k = lane; k < np; k += 32) alive += (mup[k] > 0.0);
@@ -160,6 +169,26 @@ static __device__ void shrink_sorted(const EigArgs& a, int n, int np, double eps
       }
       __syncwarp();
       --alive;
+    }
+    if (freed > 0.0 && alive > 0) {
+      // smallest alive (mass asc, position desc), as in the merges
+      double m1 = INFINITY;
+      int i1 = -1;
+      for (int k = lane; k < np; k += 32) {
+        const double v = mup[k];
+        if (v > 0.0 && ((v < m1) || (v == m1 && k > i1))) { m1 = v; i1 = k; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double om = __shfl_xor_sync(0xffffffffu, m1, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, i1, o);
+        if (oi >= 0 && (i1 < 0 || om < m1 || (om == m1 && oi > i1))) { m1 = om; i1 = oi; }
+      }
+      if (lane == 0) {
+        mup[i1] += freed;
+        dsum += freed;
+        dlast = freed;
+      }
+      __syncwarp();
     }
     if (lane == 0) { s_dsum = dsum; s_dlast = dlast; }
   }

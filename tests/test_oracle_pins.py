@@ -35,7 +35,7 @@ def test_reduce_rank_golden_cases():
     cases = json.load(open(os.path.join(HERE, "golden", "reduce_rank_cases.json")))["cases"]
     for c in cases:
         sigma = np.sqrt(np.array(c["mass"], dtype=float))
-        sp, deltas = reduce_rank(sigma, c["ell"], c["variant"], c["alpha"])
+        sp, deltas = reduce_rank(sigma, c["ell"], c["variant"], c["alpha"], c.get("mass_floor", 0.0))
         np.testing.assert_allclose(sp * sp, c["mass_prime"], rtol=1e-12, atol=1e-12,
                                    err_msg=c["name"])
         np.testing.assert_allclose(deltas, c["deltas"], rtol=1e-12, atol=1e-12,
