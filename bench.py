@@ -101,6 +101,24 @@ def config(args):
     return w
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest of every rank's x (the timed step is as slow as the slowest
+    rank); x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_batch_seed(w, rank: int) -> int:
+    """Seed of a rank's batched streams: every rank draws its own sketches
+    (sharding by sketch, no data-path collective)."""
+    return w["seed"] + 1000 * rank
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -326,7 +344,7 @@ def run_batch(args, w):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     fd.load()
     count = args.count or w["count"]
-    specs = workloads.batch_specs(count, seed=w["seed"] + 1000 * rank)
+    specs = workloads.batch_specs(count, seed=rank_batch_seed(w, rank))
     flat, views = workloads.batch_streams_device(specs)
     ds = [sp["d"] for sp in specs]
     ells = [sp["ell"] for sp in specs]
@@ -372,11 +390,7 @@ def run_batch(args, w):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     ms_kernel = sum(ka[2 * i].elapsed_time(ka[2 * i + 1]) for i in range(args.steps)) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     value = rows * world / (ms / 1e3)
 
     # end to end: host rows (a bounded copy of the device streams would not fit the
@@ -648,11 +662,7 @@ def main():
     ktimes = sk.kernel_times()
     sk.profile(False)
     clk = clocks.stop()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     value = w["n"] * world / (ms / 1e3)
     st = sk.stats()
     launches = sum(c for c, _ in ktimes.values())
