@@ -82,3 +82,21 @@ def test_bad_buffer_arguments():
         fd.FDSketch(64, 10, "fastpfd", 0.0)                   # alpha outside (0, 1]
     with pytest.raises(fd.FDError):
         fd.FDBatch([64, 64], [8, 8], "fastpfd", 0.2)          # single sketches only
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_recorded_spectrum_of_a_larger_buffer(prec):
+    """fd_record_spectrum with a buffer of 3*ell rows: last_spectrum returns
+    one value per buffer row, equal to the oracle's squared singular values of
+    the buffer at the first reduction (exactly 3*ell rows appended)."""
+    ell, L = 12, 36
+    A = W.random_noisy(L, 200, m=8, seed=97, dtype=np.float32)
+    with fd.FDSketch(200, ell, "fd", 1.0, prec, buffer_rows=L) as s:
+        s.record_spectrum()
+        s.append(torch.from_numpy(A).cuda())
+        sig2, sigp2 = s.last_spectrum()
+    assert sig2.shape == (L,) and sigp2.shape == (L,)
+    so = np.linalg.svd(A.astype(np.float64), compute_uv=False) ** 2
+    big = so >= 1e-6 * so[0]
+    tol = 2e-5 if prec == "fp32" else 2e-4
+    np.testing.assert_allclose(sig2[: so.shape[0]][big], so[big], rtol=tol)
