@@ -1,4 +1,4 @@
-// Symmetric eigensolve of the n x n buffer Gram (n = 2*ell, a full buffer) in
+// Symmetric eigensolve of the n x n buffer Gram (a full buffer, n >= 2*ell) in
 // FP32 on one CTA, for the ReduceRank step of Sec. 2.3. Only the retained
 // directions need eigenvectors, so the solve is split:
 //
@@ -10,19 +10,22 @@
 //      the trailing block and two barriers. Reflector vectors are packed, in
 //      step order, into the finished leading rows of the same buffer. The
 //      last 32 steps run on one warp with the block in registers.
-//   2. All eigenvalues of T from Sturm counts of T - x I (LDL^T pivots):
-//      one count per thread on an even grid brackets every eigenvalue, then
-//      groups of lanes refine each bracket by multisection. Values at or
-//      below the bisection's resolution, 2 eps lambda_1, count as zero.
+//   2. Eigenvalues of T from Sturm counts of T - x I (LDL^T pivots): one
+//      count per thread on an even grid brackets every eigenvalue, then
+//      groups of lanes refine each bracket by multisection. Only the ell+1
+//      largest are solved unless SS or a recorded spectrum needs all of
+//      them. Values at or below the bisection's resolution, 2 eps lambda_1,
+//      count as zero.
 //   3. For each retained position r, an eigenvector of T from a twisted
 //      factorisation of T - lambda_r I (forward and backward LDL^T pivots,
 //      twist index at the smallest |gamma|): one thread per vector, O(n).
 //   4. One Cholesky-QR pass (C = Z^T Z = L L^T, Z <- Z L^-T) makes the
-//      vectors orthonormal. If a twisted vector fails or C has a pivot
-//      below 1/4 (vectors too close to dependent, e.g. a multiple
-//      eigenvalue), every vector is recomputed by inverse iteration from a
-//      random start (pivoted LU, three solves) and orthonormalised by
-//      classical Gram-Schmidt twice.
+//      vectors orthonormal. If C has a pivot below 1/4 (vectors too close to
+//      dependent, e.g. a multiple eigenvalue), the members of clusters of
+//      close eigenvalues are recomputed by one inverse-iteration solve from a
+//      random start each (pivoted LU) and Cholesky-QR runs again; if a
+//      twisted vector failed or that fails too, every vector is recomputed
+//      that way and orthonormalised by classical Gram-Schmidt twice.
 //   5. u_r = Q z_r = H_0 ... H_{n-3} z_r with each thread holding a strided
 //      slice of one vector in registers; the rotate matrix rows
 //      sqrt(mu'_r / mu_r) u_r go straight to their destination.
