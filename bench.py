@@ -652,13 +652,20 @@ def main():
     sk.profile(True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     e0.record(stream)
-    for _ in range(args.steps):
+    ev[0].record(stream)
+    for i in range(args.steps):
         step(sk, A)
+        ev[i + 1].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
+    per_step = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps))
+    step_ms = {"median": per_step[len(per_step) // 2] if len(per_step) % 2
+               else 0.5 * (per_step[len(per_step) // 2 - 1] + per_step[len(per_step) // 2]),
+               "min": per_step[0], "max": per_step[-1]}
     ktimes = sk.kernel_times()
     sk.profile(False)
     clk = clocks.stop()
@@ -702,7 +709,10 @@ def main():
         q1.record(stream)
         torch.cuda.synchronize()
         pms = q0.elapsed_time(q1)
-        plain = {"value": w["n"] / (pms / 1e3), "unit": "rows/s", "cov_err": sp.cov_err(A)}
+        pce = sp.cov_err(A)
+        # matched error: |cov-err(mixed) - cov-err(plain)| <= 1e-5 absolute
+        plain = {"value": w["n"] / (pms / 1e3), "unit": "rows/s", "cov_err": pce,
+                 "cov_err_delta": abs(cov - pce), "matched_within_1e-5": abs(cov - pce) <= 1e-5}
         sp.close()
 
     # sharded: P contiguous shards, one handle and CUDA stream each (their
@@ -787,6 +797,7 @@ def main():
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "cov_err": cov, "reductions_per_step": st["reductions"],
         "eig_fallbacks_per_step": st.get("eig_fallbacks"),
+        "step_ms": step_ms,
         "plain_fp32": plain, "sharded": sharded,
         "roofline": roofline, "kernels": kshare,
         "gpu_launches": int(launches + 2 * args.steps),
