@@ -498,3 +498,17 @@ def test_larger_buffer(variant):
     lam = cov_spectrum(L, B)
     assert max(abs(lam[0]), abs(lam[-1])) <= 1e-10 * info["normA2"]
 
+
+
+@pytest.mark.parametrize("ell,alpha", [(20, 0.2), (12, 0.5), (10, 1.0)])
+def test_fast_alpha_fd_fixed_cadence_equals_literal(ell, alpha):
+    """For generic data a Fast alpha-FD reduction leaves exactly t-1 nonzero
+    rows, so keeping t-1 rows per reduction (the buffered form) reduces at the
+    same rows as the literal algorithm, where zero rows are free, and gives
+    the same sketch."""
+    A = W.random_noisy(800, 40, m=10, seed=89, dtype=np.float64)
+    Bb, ib = fd_sketch(A, ell, "fastpfd", alpha, "buffered")
+    Bl, il = fd_sketch(A, ell, "fastpfd", alpha, "literal")
+    assert ib["reductions"] == il["reductions"]
+    assert ib["sum_delta"] == pytest.approx(il["sum_delta"], rel=1e-10)
+    np.testing.assert_allclose(Bb.T @ Bb, Bl.T @ Bl, rtol=0, atol=1e-9 * ib["normA2"])
