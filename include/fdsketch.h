@@ -5,17 +5,19 @@
  * Guarantees". A stream of rows a_i in R^d (Sec. 1.1, notation) is summarised
  * by an ell x d sketch B whose covariance B^T B approximates A^T A; the error
  * is cov-err = ||A^T A - B^T B||_2 / ||A||_F^2 (Sec. 1.1, "Error measures").
- * The update is Algorithm 1 (Sec. 2.3) with one of four ReduceRank rules:
+ * The update is Algorithm 1 (Sec. 2.3) with one of the ReduceRank rules:
  * FD (Sec. 2.3), parameterised FD (Algorithm 2, Sec. 3.1), SpaceSaving
- * Directions (Algorithm 3, Sec. 3.1) and iterative SVD (Sec. 2.3).
+ * Directions (Algorithm 3, Sec. 3.1), iterative SVD (Sec. 2.3) and Fast
+ * alpha-FD (Sec. 3.1).
  *
- * Buffered form. The device keeps a 2*ell-row working buffer. When it is
+ * Buffered form. The device keeps a working buffer of 2*ell rows (ell for
+ * Fast alpha-FD, or the size chosen with fd_create_buffered). When it is
  * full, one reduction runs entirely on the GPU: Gram G = B B^T, symmetric
  * eigensolve G = U diag(sigma^2) U^T, the variant's sigma' (FP64), and the
- * rotate B' = diag(sigma'/sigma) U^T B, which leaves ell-1 rows. The
- * index rules use ell itself (delta = sigma_ell^2 of the 2*ell rows: Fast FD,
- * Sec. 2.3). A reduction therefore fires after the first 2*ell rows and then
- * every ell+1 rows, independent of the data.
+ * rotate B' = diag(sigma'/sigma) U^T B, which leaves ell-1 rows (t-1 for Fast
+ * alpha-FD). The index rules use ell itself (delta = sigma_ell^2 of the
+ * buffer: Fast FD, Sec. 2.3). A reduction therefore fires when the buffer is
+ * full and then every (buffer rows - rows left) rows, independent of the data.
  *
  * Conventions for every call:
  *  - Return 0 on success or a negative FD_E* code; fd_strerror() names it.
@@ -45,7 +47,9 @@ extern "C" {
  * are kept, the rest up to ell shrink by delta = sigma_ell^2, values past ell
  * are zeroed (Algorithm 2). SS: the second-smallest direction's squared value
  * is added to the smallest and the second-smallest is freed, repeated until
- * ell-1 directions remain; empty directions are freed first (Algorithm 3).
+ * ell-1 directions remain (Algorithm 3); directions whose mass is below the
+ * eigensolve's resolution are freed first and their total mass is added to
+ * the smallest retained direction, so the sketch keeps ||A||_F^2.
  * ISVD: sigma'_j = sigma_j for j < ell, else 0 (Sec. 2.3).
  * FAST_PFD (Fast alpha-FD, Sec. 3.1 "Fast Parameterized FD"): the sketch is
  * its own ell-row buffer; delta = sigma_t^2 with t = ell - ell*alpha/2
@@ -56,11 +60,17 @@ extern "C" {
 enum { FD_VAR_FD = 0, FD_VAR_PFD = 1, FD_VAR_SS = 2, FD_VAR_ISVD = 3, FD_VAR_FAST_PFD = 4 };
 
 /* Arithmetic of the reduction.
- * FD_PREC_FP32:   FP32 buffer, FP32 CUDA-core Gram and rotate, FP32 Jacobi
- *                 eigensolve; shrink and bookkeeping in FP64.
+ * FD_PREC_FP32:   FP32 buffer, FP32 CUDA-core Gram and rotate, FP32
+ *                 eigensolve (tridiagonal: Householder reduction, bisection,
+ *                 twisted-factorisation vectors, Cholesky-QR; one-sided
+ *                 Jacobi for the flush of a partial buffer); shrink and
+ *                 bookkeeping in FP64.
  * FD_PREC_BF16X3: buffer held as bfloat16 hi/lo pairs; Gram and rotate on the
  *                 tcgen05 tensor cores as split products hi*hi + hi*lo + lo*hi
- *                 accumulated in FP32 (TMEM); FP32 Jacobi; FP64 shrink.
+ *                 accumulated in FP32 (TMEM); the same FP32 eigensolve; FP64
+ *                 shrink. Its values carry about 2^-16 of rounding per
+ *                 reduction and a small low bias, which add up along
+ *                 directions that stay for thousands of reductions.
  * FD_PREC_FP64:   FP64 buffer, FP64 Gram, rotate and Jacobi (slow; for
  *                 checking against FP64 references). */
 enum { FD_PREC_FP32 = 0, FD_PREC_BF16X3 = 1, FD_PREC_FP64 = 2 };
@@ -81,7 +91,7 @@ enum {
   FD_ETOOBIG = -6  /* a size exceeds the fixed workspace of fd_cov_err_noalloc */
 };
 
-#define FD_MAX_BUFFER_ROWS 512 /* 2*ell limit of one sketch */
+#define FD_MAX_BUFFER_ROWS 512 /* buffer rows of one sketch (2*ell by default) */
 
 typedef struct fd_state* fd_handle;
 
