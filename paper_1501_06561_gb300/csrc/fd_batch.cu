@@ -5,10 +5,12 @@
 // rows) -- from a device queue ordered longest-first; the CTA that takes an
 // item runs the whole row block through Algorithm 1 (Sec. 2.3) for that
 // sketch: ingest, and at every full buffer one reduction done entirely inside
-// the CTA (Gram into shared memory, one-sided Jacobi eigensolve in shared
-// memory, FP64 ReduceRank, rotate back into the buffer). No inter-CTA
+// the CTA (Gram into shared memory; the tridiagonal eigensolve of a full
+// buffer, or block Jacobi for a partial one at a flush, both in shared memory;
+// FP64 ReduceRank; rotate back into the buffer). No inter-CTA
 // synchronisation is needed because a sketch is owned by one CTA at a time.
-// The launch is captured in a CUDA graph once per item table and replayed.
+// Each append is one item-table copy, one counter reset and one launch on the
+// batch's stream; the tile sizes below are compile-time constants.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
