@@ -270,9 +270,11 @@ int fd_destroy(fd_handle h);
  * single persistent launch in which every CTA takes work items (a sketch and a
  * block of its rows) from a device queue ordered longest-first and runs the
  * whole block through the buffered update of that sketch (ingest, Gram,
- * Jacobi eigensolve, ReduceRank, rotate) without leaving the CTA. Per sketch
- * the arithmetic and the result are those of a single handle with
- * FD_PREC_FP32. */
+ * eigensolve, ReduceRank, rotate) without leaving the CTA. Per sketch the
+ * arithmetic is that of a single handle with FD_PREC_FP32 (FP32 Gram,
+ * tridiagonal eigensolve of a full buffer and rotate, FP64 ReduceRank), and
+ * its results agree with one within rounding; the batched rotate also scales
+ * each new row to its FP64 norm sigma'_j. */
 typedef struct fd_batch_state* fd_batch;
 typedef struct {
   int32_t id;        /* sketch index, 0 <= id < count; at most once per call */

@@ -3,8 +3,11 @@
 //
 // One reduction of Algorithm 1 (Sec. 2.3) on a buffer B of n rows is
 //   G = B B^T                         (gram_simt_kernel or the tcgen05 Gram)
-//   G = U diag(sigma^2) U^T           (eig_shrink_kernel, one-sided Jacobi)
-//   sigma' = ReduceRank(sigma)        (eig_shrink_kernel, FP64)
+//   G = U diag(sigma^2) U^T           (eig_tri_kernel: FP32 tridiagonal solve of
+//                                      a full buffer; eig_fast_kernel and
+//                                      eig_shrink_kernel: one-sided Jacobi for
+//                                      a flush and for FP64)
+//   sigma' = ReduceRank(sigma)        (same kernel, FP64)
 //   B' = diag(sigma'/sigma) U^T B     (rotate_simt_kernel or the tcgen05 rotate)
 // which equals B' = S' V^T because U^T B = S V^T for the SVD B = U S V^T.
 #include <cfloat>
