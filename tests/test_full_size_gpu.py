@@ -13,10 +13,11 @@ unique at any size:
 - the removed mass of at least ell * delta per reduction.
 
 The FP32 path meets the bar. The split-precision BF16x3 path ends 4.3e-5
-above the oracle's cov-err after 1,979 reductions: the low bias of its
-tensor-core Gram adds up along directions that live through the whole
-stream, and the result also exceeds the bound Delta / ||A||_F^2. That case is
-marked as an expected failure until the bias is removed.
+above the oracle's cov-err after 1,979 reductions, which is also above the
+oracle's bound Delta / ||A||_F^2. A model of its rounding (the same split,
+exact or truncated FP32 sums) ends only 7.6e-7 above, so the cause lies in
+something that model leaves out. That case is marked as an expected failure
+until the cause is found and removed.
 """
 import json
 import os
@@ -88,8 +89,8 @@ def test_full_stream_fp32_matches_oracle(rows):
     assert ell * delta <= (st["norm_a2"] - st["sketch_norm_b2"]) * (1.0 + 1e-6)
 
 
-@pytest.mark.xfail(reason="BF16x3 low bias accumulates over 1,979 reductions: cov-err 4.3e-5 "
-                          "above the oracle's", strict=False)
+@pytest.mark.xfail(reason="BF16x3 ends 4.3e-5 above the oracle's cov-err after 1,979 "
+                          "reductions (cause not yet found)", strict=False)
 def test_full_stream_bf16x3_matches_oracle(rows):
     A, A_dev, norm2 = rows
     B, st, ce = _run(A_dev, "bf16x3")
