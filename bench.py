@@ -119,6 +119,19 @@ def rank_batch_seed(w, rank: int) -> int:
     return w["seed"] + 1000 * rank
 
 
+def mass_account(st: dict) -> dict:
+    """Bookkeeping of one sketch from its fd_stats (the latest fd_sketch's
+    totals): ||A||_F^2 - removed - ||B||_F^2 is zero in exact arithmetic, and
+    Lemma 1 (Sec. 3.1) bounds cov-err by Delta / ||A||_F^2."""
+    a2 = float(st["norm_a2"])
+    removed = float(st["sketch_removed"])
+    b2 = float(st["sketch_norm_b2"])
+    delta = float(st["sketch_sum_delta"])
+    return {"norm_a2": a2, "removed": removed, "norm_b2": b2, "sum_delta": delta,
+            "gap_rel": (a2 - removed - b2) / a2 if a2 > 0 else 0.0,
+            "lemma1_bound": delta / a2 if a2 > 0 else 0.0}
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -712,7 +725,8 @@ def main():
         pce = sp.cov_err(A)
         # matched error: |cov-err(mixed) - cov-err(plain)| <= 1e-5 absolute
         plain = {"value": w["n"] / (pms / 1e3), "unit": "rows/s", "cov_err": pce,
-                 "cov_err_delta": abs(cov - pce), "matched_within_1e-5": abs(cov - pce) <= 1e-5}
+                 "cov_err_delta": abs(cov - pce), "matched_within_1e-5": abs(cov - pce) <= 1e-5,
+                 "mass_account": mass_account(sp.stats())}
         sp.close()
 
     # sharded: P contiguous shards, one handle and CUDA stream each (their
@@ -795,7 +809,7 @@ def main():
                    "input_bytes": int(A_host.nbytes),
                    "l2": "input larger than L2 (no flush needed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "cov_err": cov, "reductions_per_step": st["reductions"],
+        "cov_err": cov, "mass_account": mass_account(st), "reductions_per_step": st["reductions"],
         "eig_fallbacks_per_step": st.get("eig_fallbacks"),
         "step_ms": step_ms,
         "plain_fp32": plain, "sharded": sharded,
