@@ -32,7 +32,7 @@ struct EigArgs {
   int nparts;
   int ldp;
   long long part_stride;  // elements between slices
-  int symmetrize;      // 1: G = (Z + Z^T) / 2 (split-precision products)
+  int symmetrize;      // informational: the load always takes G = (Z + Z^T) / 2
   int n;               // rows being reduced (2*ell, or fewer at a flush)
   int ell;
   int variant;
