@@ -132,6 +132,23 @@ def mass_account(st: dict) -> dict:
             "lemma1_bound": delta / a2 if a2 > 0 else 0.0}
 
 
+def mass_trajectory(sk, A, out, points: int = 8) -> list:
+    """mass_account at evenly spaced points of the stream A (rows appended in
+    chunks, each point read through the non-destructive sketch call): whether
+    ||A||_F^2 - removed - ||B||_F^2 grows steadily or in jumps."""
+    n = int(A.shape[0])
+    marks = sorted({max(1, int(round(n * (k + 1) / points))) for k in range(points)})
+    sk.reset()
+    done, res = 0, []
+    for mk in marks:
+        sk.append(A[done:mk])
+        done = mk
+        sk.sketch(out=out)
+        acc = mass_account(sk.stats())
+        res.append({"rows": mk, "gap_rel": acc["gap_rel"], "lemma1_bound": acc["lemma1_bound"]})
+    return res
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -688,6 +705,11 @@ def main():
     launches = sum(c for c, _ in ktimes.values())
     # accuracy of this run: cov-err of the sketch against the whole stream
     cov = sk.cov_err(A)
+    # bookkeeping along the stream (untimed; its own pass over the rows)
+    try:
+        trajectory = mass_trajectory(sk, A, B)
+    except Exception as ex:  # a diagnostic: never cost the result line
+        trajectory = {"error": f"{type(ex).__name__}: {ex}"}
 
     # end to end through host buffers (pinned staging and copies inside)
     e2e = None
@@ -809,7 +831,8 @@ def main():
                    "input_bytes": int(A_host.nbytes),
                    "l2": "input larger than L2 (no flush needed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "cov_err": cov, "mass_account": mass_account(st), "reductions_per_step": st["reductions"],
+        "cov_err": cov, "mass_account": mass_account(st), "mass_trajectory": trajectory,
+        "reductions_per_step": st["reductions"],
         "eig_fallbacks_per_step": st.get("eig_fallbacks"),
         "step_ms": step_ms,
         "plain_fp32": plain, "sharded": sharded,
