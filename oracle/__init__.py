@@ -13,6 +13,7 @@ from .fd_oracle import (  # noqa: F401
     cov_spectrum,
     fast_pfd_split,
     fd_sketch,
+    jacobi_svd_rows,
     proj_err,
     reduce_rank,
     shrink_index_split,

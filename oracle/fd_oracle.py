@@ -9,7 +9,8 @@ What it follows
   scaled right singular vectors ``S' V^T`` of the rows seen so far; when no
   free (zero) row is left, take ``[U, S, V] = svd(B)``, apply ReduceRank to
   ``S`` and set ``B = S' V^T``. The ``svd`` step is numpy's LAPACK SVD, used as
-  a library primitive.
+  a library primitive, or (``svd="jacobi"``) the oracle's own one-sided
+  Jacobi SVD of the buffer rows; the two are pinned against each other.
 * ReduceRank rules:
     - iSVD (Sec. 2.3): keep ``sigma_j`` for ``j < ell``, zero ``sigma_ell``.
     - FD   (Sec. 2.3): ``sigma'_j = sqrt(sigma_j^2 - delta)``,
@@ -169,15 +170,84 @@ def reduce_rank(sigma, ell: int, variant: str, alpha: float = 1.0,
     raise ValueError(f"unknown variant {variant!r}")
 
 
-def _svd_rows(X: np.ndarray):
+def jacobi_svd_rows(X: np.ndarray, tol: float = 1e-15, max_sweeps: int = 60):
+    """The oracle's own SVD of the rows of ``X``: one-sided (Hestenes) Jacobi.
+
+    Pairs of rows ``(r_p, r_q)`` are rotated in their plane until every pair
+    is orthogonal, ``|<r_p, r_q>| <= tol * ||r_p|| ||r_q||`` (Hestenes 1958).
+    A rotation by the angle that zeroes ``<r_p, r_q>``: with
+    ``a = ||r_p||^2, b = ||r_q||^2, g = <r_p, r_q>``, ``zeta = (b - a) / (2 g)``,
+    ``t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2))``, ``c = 1 / sqrt(1 + t^2)``,
+    ``s = c t``: ``r_p <- c r_p - s r_q``, ``r_q <- s r_p + c r_q``. The pairs
+    of one sweep are visited in round-robin rounds of disjoint pairs (the
+    rows of a round are independent, so a round is one vector operation).
+    Then ``sigma_j = ||r_j||`` and ``v_j = r_j / sigma_j``, sorted by sigma
+    descending (ties by row index).
+
+    Returns ``(sigma, V, sweeps)``; V has zero rows where sigma is zero.
+    """
+    R = np.array(X, dtype=np.float64, copy=True)
+    m, d = R.shape
+    if m == 0:
+        return np.zeros(0), np.zeros((0, d)), 0
+    mp = m + (m & 1)
+    if mp != m:
+        R = np.vstack([R, np.zeros((1, d))])
+    # rows whose squared norm is at the FP64 resolution of the matrix are
+    # numerically zero: rotating them only moves rounding noise around
+    zfloor = (max(m, d) * np.finfo(np.float64).eps * np.sqrt(np.sum(R * R))) ** 2
+    sweeps = 0
+    for sweeps in range(1, max_sweeps + 1):
+        rotated = False
+        for r in range(mp - 1):
+            # round r: position 0 fixed, the others rotate by one place
+            idx = [0] + [1 + (k - 1 + r) % (mp - 1) for k in range(1, mp)]
+            P = np.array(idx[: mp // 2])
+            Q = np.array(idx[mp // 2:][::-1])
+            rp, rq = R[P], R[Q]
+            a = np.einsum("ij,ij->i", rp, rp)
+            b = np.einsum("ij,ij->i", rq, rq)
+            g = np.einsum("ij,ij->i", rp, rq)
+            act = (np.abs(g) > tol * np.sqrt(a * b)) & (a > zfloor) & (b > zfloor)
+            if not np.any(act):
+                continue
+            rotated = True
+            gg = np.where(act, g, 1.0)
+            zeta = (b - a) / (2.0 * gg)
+            t = np.sign(zeta) / (np.abs(zeta) + np.sqrt(1.0 + zeta * zeta))
+            t = np.where(zeta == 0.0, 1.0, t)
+            c = 1.0 / np.sqrt(1.0 + t * t)
+            sn = c * t
+            c = np.where(act, c, 1.0)[:, None]
+            sn = np.where(act, sn, 0.0)[:, None]
+            R[P], R[Q] = c * rp - sn * rq, sn * rp + c * rq
+        if not rotated:
+            break
+    R = R[:m]
+    norms = np.sqrt(np.einsum("ij,ij->i", R, R))
+    order = sorted(range(m), key=lambda j: (-norms[j], j))
+    sigma = norms[order]
+    V = np.zeros((m, d))
+    for k, j in enumerate(order):
+        if norms[j] > 0.0:
+            V[k] = R[j] / norms[j]
+    return sigma, V, sweeps
+
+
+def _svd_rows(X: np.ndarray, method: str = "lapack"):
     """Singular values (descending, padded to the row count) and right vectors.
 
     Returns ``(sigma, V)`` with ``V`` of shape ``(rows, d)``; rows of ``V``
     past ``min(rows, d)`` are zero (their singular value is zero too).
+    ``method``: ``"lapack"`` (numpy's SVD, a library primitive) or
+    ``"jacobi"`` (the oracle's own one-sided Jacobi, ``jacobi_svd_rows``).
     """
     m, d = X.shape
     if m == 0:
         return np.zeros(0), np.zeros((0, d))
+    if method == "jacobi":
+        sigma, V, _ = jacobi_svd_rows(X)
+        return sigma, V
     _, s, vt = np.linalg.svd(X, full_matrices=False)
     k = s.shape[0]
     sigma = np.zeros(m)
@@ -197,7 +267,8 @@ class FDOracle:
     """
 
     def __init__(self, d: int, ell: int, variant: str = "fd", alpha: float = 1.0,
-                 mode: str = "buffered", record: bool = False, buffer_rows: int | None = None):
+                 mode: str = "buffered", record: bool = False, buffer_rows: int | None = None,
+                 svd: str = "lapack"):
         if variant not in VARIANTS:
             raise ValueError(variant)
         if ell < 2 or d < 1:
@@ -206,6 +277,9 @@ class FDOracle:
             raise ValueError("alpha must lie in (0, 1]")
         if mode not in ("buffered", "literal"):
             raise ValueError(mode)
+        if svd not in ("lapack", "jacobi"):
+            raise ValueError(svd)
+        self.svd = svd
         self.d, self.ell, self.variant, self.mode = d, ell, variant, mode
         self.alpha = alpha if variant in ("pfd", "fastpfd") else 1.0
         if variant == "fastpfd":
@@ -242,7 +316,7 @@ class FDOracle:
         retained rows ``sigma'_j v_j`` ordered by ``sigma'`` descending
         (stable in the slot index).
         """
-        sigma, V = _svd_rows(X)
+        sigma, V = _svd_rows(X, self.svd)
         # numerical-rank floor of the FP64 SVD (largest value x size x eps),
         # squared: masses at or below it are treated as exactly zero (SS)
         floor = (sigma[0] * max(X.shape) * np.finfo(np.float64).eps) ** 2 if sigma.size else 0.0
@@ -376,13 +450,14 @@ class FDOracle:
 
 
 def fd_sketch(A, ell: int, variant: str = "fd", alpha: float = 1.0,
-              mode: str = "buffered", record: bool = False, buffer_rows: int | None = None):
+              mode: str = "buffered", record: bool = False, buffer_rows: int | None = None,
+              svd: str = "lapack"):
     """Run the whole stream ``A`` (rows in order) and return ``(B, info)``.
 
     With ``record=True`` the per-reduction records are in ``info["records"]``.
     """
     A = np.asarray(A)
-    o = FDOracle(A.shape[1], ell, variant, alpha, mode, record, buffer_rows)
+    o = FDOracle(A.shape[1], ell, variant, alpha, mode, record, buffer_rows, svd)
     o.append(A)
     B, info = o.sketch()
     if record:

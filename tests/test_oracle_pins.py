@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 from oracle import (FDOracle, compensate, cov_err, cov_spectrum, fast_pfd_split, fd_sketch,
-                    proj_err, reduce_rank)
+                    jacobi_svd_rows, proj_err, reduce_rank)
 from paper_1501_06561_gb300 import workloads as W
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -512,3 +512,47 @@ def test_fast_alpha_fd_fixed_cadence_equals_literal(ell, alpha):
     assert ib["reductions"] == il["reductions"]
     assert ib["sum_delta"] == pytest.approx(il["sum_delta"], rel=1e-10)
     np.testing.assert_allclose(Bb.T @ Bb, Bl.T @ Bl, rtol=0, atol=1e-9 * ib["normA2"])
+
+
+# --------------------------------------------------------------------------
+# The oracle's own SVD (one-sided Jacobi) against the textbook SVD and a
+# closed form; whole streams through either SVD route agree
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("m,d", [(5, 8), (20, 64), (64, 64), (40, 30), (1, 7)])
+def test_jacobi_svd_matches_textbook_svd(m, d):
+    rng = np.random.default_rng(100 + m + d)
+    X = rng.standard_normal((m, d)) * np.logspace(3, 0, m)[:, None]  # graded rows
+    sigma, V, sweeps = jacobi_svd_rows(X)
+    ref = np.linalg.svd(X, compute_uv=False)
+    k = min(m, d)
+    np.testing.assert_allclose(sigma[:k], ref, rtol=1e-12, atol=1e-12 * ref[0])
+    assert np.all(np.abs(sigma[k:]) <= 1e-12 * ref[0])
+    live = sigma > 1e-12 * ref[0]
+    Vl = V[live]
+    np.testing.assert_allclose(Vl @ Vl.T, np.eye(Vl.shape[0]), atol=1e-13)
+    # X^T X = V^T diag(sigma^2) V (the right vectors span the row space)
+    np.testing.assert_allclose(Vl.T @ np.diag(sigma[live] ** 2) @ Vl, X.T @ X,
+                               atol=1e-12 * ref[0] ** 2)
+    assert sweeps < 60
+
+
+def test_jacobi_svd_closed_form():
+    """Rows 3 q_1, 2 q_2, 1 q_3 of orthonormal q, mixed by a rotation: sigma = 3, 2, 1."""
+    q, _ = np.linalg.qr(np.random.default_rng(7).standard_normal((6, 3)))
+    c, s = math.cos(0.3), math.sin(0.3)
+    mix = np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+    X = mix @ (np.diag([3.0, 2.0, 1.0]) @ q.T)
+    sigma, V, _ = jacobi_svd_rows(X)
+    np.testing.assert_allclose(sigma, [3.0, 2.0, 1.0], rtol=1e-14)
+    np.testing.assert_allclose(np.abs(V @ q), np.eye(3), atol=1e-13)
+
+
+@pytest.mark.parametrize("variant", ["fd", "pfd", "isvd", "ss"])
+def test_stream_through_jacobi_svd_equals_lapack_route(variant):
+    A = W.random_noisy(400, 48, m=8, seed=55, dtype=np.float64)
+    Bl, il = fd_sketch(A, 6, variant, _alpha(variant))
+    Bj, ij = fd_sketch(A, 6, variant, _alpha(variant), svd="jacobi")
+    np.testing.assert_allclose(np.linalg.svd(Bj, compute_uv=False),
+                               np.linalg.svd(Bl, compute_uv=False), rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(Bj.T @ Bj, Bl.T @ Bl, atol=1e-9 * il["normA2"])
+    assert abs(ij["sum_delta"] - il["sum_delta"]) <= 1e-10 * il["normA2"]
