@@ -679,7 +679,6 @@ def main():
     barrier()
     torch.cuda.synchronize()
     clocks.start()
-    sk.profile(True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
@@ -696,13 +695,17 @@ def main():
     step_ms = {"median": per_step[len(per_step) // 2] if len(per_step) % 2
                else 0.5 * (per_step[len(per_step) // 2 - 1] + per_step[len(per_step) // 2]),
                "min": per_step[0], "max": per_step[-1]}
+    clk = clocks.stop()
+    # per-kernel device times from one more step, outside the timed region
+    # (the events bracketing every launch would otherwise be timed too)
+    sk.profile(True)
+    step(sk, A)
     ktimes = sk.kernel_times()
     sk.profile(False)
-    clk = clocks.stop()
     ms = max_over_ranks(ms, world)
     value = w["n"] * world / (ms / 1e3)
     st = sk.stats()
-    launches = sum(c for c, _ in ktimes.values())
+    launches = sum(c for c, _ in ktimes.values()) * args.steps
     # accuracy of this run: cov-err of the sketch against the whole stream
     cov = sk.cov_err(A)
     # bookkeeping along the stream (untimed; its own pass over the rows)
@@ -810,7 +813,7 @@ def main():
                 # eigensolve runs on one SM: its share of the chip's peak
                 "per_sm": {"peak": sm_peak,
                            "frac": (achieved / sm_peak) if achieved else None}}
-    kshare = {k: {"launches": c, "ms_per_step": m / args.steps,
+    kshare = {k: {"launches": c, "ms_per_step": m,
                   "share": (m / sum(x for _, x in ktimes.values())) if ktimes else None}
               for k, (c, m) in ktimes.items()}
     cpu = None

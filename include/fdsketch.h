@@ -183,6 +183,24 @@ int fd_sketch_compensated(fd_handle h, void* out, int32_t dtype, int32_t out_on_
  * different d), FD_ECUDA. */
 int fd_merge(fd_handle dst, fd_handle src);
 
+/* fd_merge for a source sketch that lives elsewhere (another process or GPU,
+ * a file): the same result as fd_merge(dst, src) when B holds the rows of
+ * src's sketch (as fd_sketch returns them, up to its last nonzero row) and
+ * *src the counters fd_stats gave for src after that fd_sketch call. This is
+ * the exchange step of a stream split across GPUs (Sec. 1, distributed
+ * streams): each GPU sketches its part, the rows and counters are gathered,
+ * and one GPU folds them in with this call (Lemma 1, Sec. 3.1, then bounds
+ * the union by the sum of all deltas).
+ * B: rows x d values of `dtype`, row stride ld, device (on_device != 0) or
+ * host memory; 0 <= rows <= dst's ell. From *src: d (must equal dst's),
+ * n_seen (>= rows), norm_a2 (||A||_F^2 of the source stream, which replaces
+ * the squared norms of the appended rows in dst's ||A||_F^2),
+ * sketch_sum_delta and sketch_removed (added to dst's Delta and removed
+ * mass) and reductions (added). Synchronises dst's stream.
+ * Errors: FD_EINVAL (null, size or width mismatch), FD_ECUDA. */
+int fd_merge_sketch(fd_handle dst, const void* B, int64_t rows, int64_t ld, int32_t dtype,
+                    int32_t on_device, const fd_stats_t* src);
+
 /* cov-err(A, B) = ||A^T A - B^T B||_2 / ||A||_F^2 (Sec. 1.1) for the handle's
  * current sketch B (as fd_sketch returns it) and the n x d matrix A, with
  * ||.||_2 = max |eigenvalue| (Sec. 1.1, the maximum of |(||Ax||^2 - ||Bx||^2)|

@@ -37,12 +37,12 @@ size_t tri_global_workspace(int n);
 
 // tensor-core path (fd_tc.cu)
 struct TcCtx;
-int tc_create(TcCtx** out, int64_t d, int ell, int L, cudaStream_t st);
+int tc_create(TcCtx** out, int64_t d, int ell, int L, int keep, cudaStream_t st);
 void tc_destroy(TcCtx* t);
 int tc_ingest(TcCtx* t, const void* src, int64_t n, int64_t ld, int dtype, int row0,
-              double* rownorm, DevCounters* ctr);
+              double* rownorm, DevCounters* ctr, double* part);
 int tc_gram(TcCtx* t, int nrows);
-int tc_eig(TcCtx* t, const EigArgs& eig_template);
+int tc_eig(TcCtx* t, const EigArgs& eig_template, int commit);
 int tc_rotate(TcCtx* t, int nrows, int write_sketch, float* sketch_out, int64_t ldo);
 int tc_export_rows(TcCtx* t, int rows, float* out, int64_t ldo);
 int tc_error(TcCtx* t);
@@ -76,6 +76,7 @@ struct fd_state {
   int64_t n_seen = 0;
 
   void* parts = nullptr;  // Gram partial slices
+  void* gsum = nullptr;   // their sum, symmetrised (L x L)
   int ldp = 0;
   int ksplit = 1;
   int keep = 0;  // rows a reduction leaves in the buffer
@@ -87,9 +88,15 @@ struct fd_state {
   void* sk = nullptr;     // flush output, ell x ldb
   void* outdev = nullptr; // conversion scratch for host output, ell x d doubles
 
+  float* gsave = nullptr;  // eigensolve refinement: the scaled Gram (L x ldg)
+  int ldg = 0;
+  float* uvec = nullptr;   // and the unscaled vectors ((ell+1) x L)
+
   DevCounters* ctr = nullptr;
   DevCounters* ctr_flush = nullptr;
   double* rownorm = nullptr;
+  double* ing_part = nullptr;  // tile ingest: partial squared norms
+  int* ing_err = nullptr;      // tile ingest: a bounded TMA wait gave up
   double* sig2 = nullptr;
   double* sigp2 = nullptr;
   bool flushed = false;
@@ -102,6 +109,7 @@ struct fd_state {
   int stage_next = 0;
   DevCounters* hctr = nullptr;  // pinned copy for fd_stats
   int* dint = nullptr;          // device int (merge: rows of the sketch)
+  double* merge_tmp = nullptr;  // device double (fd_merge_sketch: ||A||_F^2 before the rows)
   int* hint = nullptr;          // pinned copy
 
   TcCtx* tc = nullptr;    // tensor-core planes (FD_PREC_BF16X3)
@@ -167,17 +175,23 @@ static void free_state(fd_state* h) {
     if (h->stage_ev[i]) cudaEventDestroy(h->stage_ev[i]);
   }
   cudaFree(h->parts);
+  cudaFree(h->gsum);
   cudaFree(h->work);
+  cudaFree(h->gsave);
+  cudaFree(h->uvec);
   cudaFree(h->wrot);
   cudaFree(h->sk);
   cudaFree(h->outdev);
   cudaFree(h->ctr);
   cudaFree(h->ctr_flush);
   cudaFree(h->rownorm);
+  cudaFree(h->ing_part);
+  cudaFree(h->ing_err);
   cudaFree(h->sig2);
   cudaFree(h->sigp2);
   if (h->hctr) cudaFreeHost(h->hctr);
   cudaFree(h->dint);
+  cudaFree(h->merge_tmp);
   if (h->hint) cudaFreeHost(h->hint);
   if (h->tc) tc_destroy(h->tc);
   delete h;
@@ -252,16 +266,22 @@ extern "C" int fd_create_buffered(int64_t d, int32_t ell, int32_t variant, doubl
     h->ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(kt, 304 / (tiles * tiles)));
     const int slices = gram_simt_slices(d, h->ksplit);
     FD_ALLOC(h->parts, (size_t)slices * h->ldp * h->ldp * h->es);
+    FD_ALLOC(h->gsum, (size_t)h->ldp * h->ldp * h->es);
     size_t wb = eig_fits_smem(h->L, h->es) ? 0 : (size_t)(np + 1) * (np + 1) * h->es;
     if (prec == FD_PREC_FP32 && tri_config(h->L, ell) == 4)
       wb = std::max(wb, tri_global_workspace(h->L));
     if (wb) { FD_ALLOC(h->work, wb); h->work_bytes = wb; }
   } else {
-    int rc = tc_create(&h->tc, d, ell, h->L, h->st);
+    int rc = tc_create(&h->tc, d, ell, h->L, h->keep, h->st);
     if (rc != FD_OK) { free_state(h); return rc; }
     size_t wb = eig_fits_smem(h->L, 4) ? 0 : (size_t)(np + 1) * (np + 1) * 4;
     if (tri_config(h->L, ell) == 4) wb = std::max(wb, tri_global_workspace(h->L));
     if (wb) { FD_ALLOC(h->work, wb); h->work_bytes = wb; }
+  }
+  if (prec != FD_PREC_FP64 && tri_config(h->L, ell) != 0) {
+    h->ldg = (h->L + 3) & ~3;
+    FD_ALLOC(h->gsave, (size_t)h->L * h->ldg * 4);
+    FD_ALLOC(h->uvec, (size_t)(ell + 4) * h->L * 4);  // also G U, L x ((ell+1) rounded to 4)
   }
   h->ldr = (h->L + 63) / 64 * 64;
   FD_ALLOC(h->wrot, (size_t)ell * h->ldr * h->es);
@@ -270,7 +290,10 @@ extern "C" int fd_create_buffered(int64_t d, int32_t ell, int32_t variant, doubl
   FD_ALLOC(h->ctr, sizeof(DevCounters));
   FD_ALLOC(h->ctr_flush, sizeof(DevCounters));
   FD_ALLOC(h->rownorm, (size_t)FD_MAX_BUFFER_ROWS * 8);
+  FD_ALLOC(h->ing_part, ingest_part_bytes(d, h->L));
+  FD_ALLOC(h->ing_err, sizeof(int));
   FD_ALLOC(h->dint, 16);
+  FD_ALLOC(h->merge_tmp, 8);
   FD_ALLOC(h->sig2, (size_t)FD_MAX_BUFFER_ROWS * 8);
   FD_ALLOC(h->sigp2, (size_t)FD_MAX_BUFFER_ROWS * 8);
 #undef FD_ALLOC
@@ -299,13 +322,22 @@ static int reduce_rows(fd_state* h, int nrows, void* out, int64_t ldo, DevCounte
                        bool diag) {
   EigArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.n = nrows;
+  // A flush of a partial buffer is solved at the full buffer size, its
+  // missing rows taken as zero, so that it gets the same eigensolve (and
+  // refinement) as a full reduction; FP64 and buffers the tridiagonal solve
+  // does not take keep the one-sided Jacobi on the rows present.
+  const bool tri = h->prec != FD_PREC_FP64 && tri_config(h->L, h->ell) != 0;
+  a.n = tri ? h->L : nrows;
+  a.nvalid = nrows;
   a.ell = h->ell;
   a.variant = h->variant;
   a.alpha = h->alpha;
   a.work = h->work;
   a.work_bytes = h->work_bytes;
-  a.ldw_work = nrows + (nrows & 1);
+  a.ldw_work = a.n + (a.n & 1);
+  a.gsave = h->gsave;
+  a.ldgsave = h->ldg;
+  a.uvec = h->uvec;
   a.ctr_in = h->ctr;
   a.ctr_out = ctr_out;
   a.sig2_out = (diag && h->record_spectrum) ? h->sig2 : nullptr;
@@ -315,27 +347,30 @@ static int reduce_rows(fd_state* h, int nrows, void* out, int64_t ldo, DevCounte
   a.max_sweeps = h->max_sweeps;
   a.tol = h->tol;
   a.symmetrize = 1;
-  a.use_tri = (nrows == h->L) ? 1 : 0;  // flushes of a partial buffer keep Jacobi
+  a.use_tri = tri ? 1 : 0;
   if (h->prec == FD_PREC_BF16X3) {
     int rc;
     { ProfScope ps(h, FD_K_GRAM); rc = tc_gram(h->tc, nrows); }
     if (rc != FD_OK) return rc;
-    { ProfScope ps(h, FD_K_EIG); rc = tc_eig(h->tc, a); }
+    { ProfScope ps(h, FD_K_EIG); rc = tc_eig(h->tc, a, out == nullptr ? 1 : 0); }
     if (rc != FD_OK) return rc;
     { ProfScope ps(h, FD_K_ROTATE);
       rc = tc_rotate(h->tc, nrows, out != nullptr ? 1 : 0, reinterpret_cast<float*>(out), ldo); }
     return rc;
   }
   const int slices = gram_simt_slices(h->d, h->ksplit);
-  a.parts = h->parts;
-  a.nparts = slices;
+  a.parts = h->gsum;
+  a.nparts = 1;
   a.ldp = h->ldp;
   a.part_stride = (long long)h->ldp * h->ldp;
   if (h->prec == FD_PREC_FP64) {
     const double* B = reinterpret_cast<const double*>(h->buf[h->cur]);
     { ProfScope ps(h, FD_K_GRAM);
       FD_CK((launch_gram_simt<double>(B, h->ldb, nrows, h->d, reinterpret_cast<double*>(h->parts),
-                                      h->ldp, h->ksplit, h->st))); }
+                                      h->ldp, h->ksplit, h->st)));
+      FD_CK((launch_gram_sum_parts<double>(reinterpret_cast<const double*>(h->parts), slices,
+                                           h->ldp, nrows, reinterpret_cast<double*>(h->gsum),
+                                           h->ldp, h->st))); }
     { ProfScope ps(h, FD_K_EIG);
       FD_CK(launch_eig_shrink<double>(a, h->st)); }
     { ProfScope ps(h, FD_K_ROTATE);
@@ -346,7 +381,10 @@ static int reduce_rows(fd_state* h, int nrows, void* out, int64_t ldo, DevCounte
     const float* B = reinterpret_cast<const float*>(h->buf[h->cur]);
     { ProfScope ps(h, FD_K_GRAM);
       FD_CK((launch_gram_simt<float>(B, h->ldb, nrows, h->d, reinterpret_cast<float*>(h->parts),
-                                     h->ldp, h->ksplit, h->st))); }
+                                     h->ldp, h->ksplit, h->st)));
+      FD_CK((launch_gram_sum_parts<float>(reinterpret_cast<const float*>(h->parts), slices,
+                                          h->ldp, nrows, reinterpret_cast<float*>(h->gsum),
+                                          h->ldp, h->st))); }
     { ProfScope ps(h, FD_K_EIG);
       FD_CK(launch_eig_shrink<float>(a, h->st)); }
     { ProfScope ps(h, FD_K_ROTATE);
@@ -366,13 +404,19 @@ static int append_device(fd_state* h, const char* src, int64_t n, int64_t ld, in
     const int c = (int)std::min<int64_t>(n - i, h->L - h->m);
     ProfScope* ps = new ProfScope(h, FD_K_INGEST);
     if (h->prec == FD_PREC_BF16X3) {
-      int rc = tc_ingest(h->tc, src + i * rb, c, ld, dtype, h->m, h->rownorm, h->ctr);
+      int rc = tc_ingest(h->tc, src + i * rb, c, ld, dtype, h->m, h->rownorm, h->ctr,
+                         h->ing_part);
       if (rc != FD_OK) return rc;
+    } else if (h->prec == FD_PREC_FP32) {
+      FD_CK(launch_ingest_tiles(src + i * rb, c, ld, dtype,
+                                reinterpret_cast<float*>(h->buf[h->cur]), h->ldb, h->d, h->m,
+                                nullptr, nullptr, 0, nullptr, nullptr, 0, h->ing_part,
+                                h->rownorm, nullptr, h->ctr, &h->ctr->ingest_ticket, h->ing_err,
+                                h->st));
     } else {
       char* dst = reinterpret_cast<char*>(h->buf[h->cur]) + (size_t)h->m * h->ldb * h->es;
-      FD_CK(launch_ingest(src + i * rb, c, ld, dtype, dst, h->ldb, h->prec == FD_PREC_FP64,
-                          h->d, h->rownorm, h->ctr, nullptr, nullptr, 0, nullptr, nullptr, 0,
-                          h->m, h->st));
+      FD_CK(launch_ingest(src + i * rb, c, ld, dtype, dst, h->ldb, 1, h->d, h->rownorm, h->ctr,
+                          nullptr, nullptr, 0, nullptr, nullptr, 0, h->m, h->st));
     }
     delete ps;
     h->m += c;
@@ -509,6 +553,28 @@ extern "C" int fd_merge(fd_handle dst, fd_handle src) {
   return FD_OK;
 }
 
+extern "C" int fd_merge_sketch(fd_handle dst, const void* B, int64_t rows, int64_t ld,
+                               int32_t dtype, int32_t on_device, const fd_stats_t* src) {
+  if (!dst || !src || rows < 0 || (rows > 0 && (!B || ld < dst->d)) || dtype_size(dtype) == 0)
+    return FD_EINVAL;
+  if (rows > dst->ell) return FD_EINVAL;  // a sketch has at most ell rows
+  if (src->n_seen < rows || src->d != dst->d) return FD_EINVAL;
+  FD_CK(cudaMemcpyAsync(dst->merge_tmp, &dst->ctr->norm_a2, sizeof(double),
+                        cudaMemcpyDeviceToDevice, dst->st));
+  dst->flushed = false;
+  if (rows > 0) {
+    // the sketch rows enter dst's stream as ordinary rows (as in fd_merge)
+    int rc = fd_append(dst, B, rows, ld, dtype, on_device);
+    if (rc != FD_OK) return rc;
+  }
+  FD_CK(launch_merge_counters_values(dst->ctr, dst->merge_tmp, src->norm_a2,
+                                     src->sketch_sum_delta, src->sketch_removed,
+                                     src->reductions, dst->st));
+  dst->n_seen += src->n_seen - rows;
+  FD_CK(cudaStreamSynchronize(dst->st));
+  return FD_OK;
+}
+
 extern "C" int fd_stats(fd_handle h, fd_stats_t* s) {
   if (!h || !s) return FD_EINVAL;
   FD_CK(cudaMemcpyAsync(h->hctr, h->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, h->st));
@@ -518,6 +584,14 @@ extern "C" int fd_stats(fd_handle h, fd_stats_t* s) {
   if (h->tc && tc_error(h->tc)) {
     set_cuda_error(cudaErrorLaunchTimeout, "tensor-core pipeline wait gave up");
     return FD_ECUDA;
+  }
+  {
+    int ie = 0;
+    FD_CK(cudaMemcpy(&ie, h->ing_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (ie) {
+      set_cuda_error(cudaErrorLaunchTimeout, "ingest TMA wait gave up");
+      return FD_ECUDA;
+    }
   }
   const DevCounters& c = h->hctr[0];
   const DevCounters& f = h->hctr[1];

@@ -374,7 +374,7 @@ int run_lanczos(const TA* A, int64_t n, int64_t d, int64_t lda, const TB* B, int
     normalize_kernel<<<dblocks, CE_THREADS, 0, st>>>(w, c, V + (size_t)(j + 1) * d, be + j, d);
     k = j + 1;
     const bool last = (k == kmax);
-    if (k >= 4 && ((k % 8) == 0 || last)) {
+    if ((k >= 4 && (k % 8) == 0) || last) {  // always check at the last step (d < 4 too)
       const int nres = topk > 0 ? 2 * topk : 4;
       if (topk > 0)
         tri_topk_kernel<<<1, ((topk + 31) / 32) * 32, 0, st>>>(al, be, k, topk, sc, res);
@@ -507,7 +507,13 @@ int run_proj(const TA* A, int64_t n, int64_t d, int64_t lda, const double* R, in
   if (e != cudaSuccess) { set_cuda_error(e, "proj-err kernels"); return FD_ECUDA; }
   double topsum = 0.0;
   for (int i = 0; i < k; ++i) topsum += top[i];
-  const double num = na2 - cap, den = na2 - topsum;
+  // A of rank at most k (k >= d, or a denominator at the Lanczos run's
+  // resolution of 1e-10 ||A||_F^2 per value) has ||A - A_k||_F^2 = 0; the
+  // ratio is then 1 when B_k captures A as well (a numerator at the
+  // resolution of the FP32 products), and unbounded otherwise
+  double num = na2 - cap, den = (k >= d) ? 0.0 : na2 - topsum;
+  if (den <= 10.0 * k * 1e-10 * na2) den = 0.0;
+  if (den == 0.0 && num <= 1e-6 * na2) num = 0.0;
   if (num_out) *num_out = num;
   if (den_out) *den_out = den;
   if (den <= 0.0) *pe = (num <= 0.0) ? 1.0 : INFINITY;

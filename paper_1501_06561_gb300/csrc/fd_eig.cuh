@@ -34,24 +34,62 @@ inline size_t eig_scalar_bytes(int np) {
   return (size_t)np * (4 * sizeof(double) + 2 * sizeof(int)) + 256;
 }
 
+// The exact diagonal of a tensor-core buffer (EigArgs.diag64 set): FP64
+// squared norms of the stored rows, the rotate's partial sums added in a
+// fixed order for rows 0..nret-1. Ends with a block barrier.
+__device__ inline void eig_prepare_diag(const EigArgs& a, int n) {
+  if (a.diag64 != nullptr) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double dg;
+      if (a.nvalid > 0 && i >= a.nvalid) {
+        dg = 0.0;  // padding rows of a flush
+      } else if (i < a.nret) {
+        dg = 0.0;
+        for (int p = 0; p < a.rot_nparts; ++p) dg += a.rot_part[(int64_t)p * a.rot_ld + i];
+      } else {
+        dg = a.slot_n2[i];
+      }
+      a.diag64[i] = dg;
+    }
+  }
+  __syncthreads();
+}
+
 // Load G = sum of the partial slices (fixed order), symmetrised, into Wm
-// (column j = row j of the symmetric G, stride ld, zero padding to np).
+// (column j = row j of the symmetric G, stride ld, zero padding to np),
+// with the exact diagonal when eig_prepare_diag supplied one.
 template <typename T>
 __device__ void eig_load(const EigArgs& a, T* Wm, int ld, int n, int np) {
   const T* parts = reinterpret_cast<const T*>(a.parts);
+  const int nv = (a.nvalid > 0 && a.nvalid < n) ? a.nvalid : n;  // rows holding data
   for (int idx = threadIdx.x; idx < np * ld; idx += blockDim.x) {
     const int i = idx / ld, j = idx - (idx / ld) * ld;
     T v = T(0);
-    if (i < n && j < n) {
-      T sij = T(0), sji = T(0);
-      for (int p = 0; p < a.nparts; ++p) {
-        sij += parts[(int64_t)p * a.part_stride + (int64_t)i * a.ldp + j];
-        sji += parts[(int64_t)p * a.part_stride + (int64_t)j * a.ldp + i];
+    if (i < nv && j < nv) {
+      if (a.diag64 != nullptr && i == j) {
+        v = (T)a.diag64[i];
+      } else {
+        T sij = T(0), sji = T(0);
+        for (int p = 0; p < a.nparts; ++p) {
+          sij += parts[(int64_t)p * a.part_stride + (int64_t)i * a.ldp + j];
+          sji += parts[(int64_t)p * a.part_stride + (int64_t)j * a.ldp + i];
+        }
+        v = T(0.5) * (sij + sji);
       }
-      v = T(0.5) * (sij + sji);
     }
     Wm[(int64_t)i * ld + j] = v;
   }
+}
+
+// FP64 trace of the loaded G: the exact diagonal when it is known, else the
+// diagonal of Wm (scaled back by wscale). One warp (threads 0..31); the
+// result is valid in lane 0.
+template <typename T>
+__device__ double eig_trace(const EigArgs& a, const T* Wm, int ld, int n, double wscale) {
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += 32)
+    t += (a.diag64 != nullptr) ? a.diag64[i] : (double)Wm[(size_t)i * ld + i] * wscale;
+  return warp_sum(t);
 }
 
 // Steps after the Jacobi sweeps: eigenvalues, sort, ReduceRank (FP64),
@@ -347,7 +385,17 @@ __device__ void eig_finish(const EigArgs& a, const T* Wm, int ld, int n, int np,
     }
   }
 
-  write_counters(a, n, mu, mup, s_count, s_ds, s_dl, capped, sweep);
+  double tr = -1.0;
+  if (a.diag64 != nullptr) {
+    __shared__ double s_tr;
+    if (tid < 32) {
+      const double t = eig_trace(a, Wm, ld, n, wscale);
+      if (tid == 0) s_tr = t;
+    }
+    __syncthreads();
+    tr = s_tr;
+  }
+  write_counters(a, n, mu, mup, s_count, s_ds, s_dl, capped, sweep, tr);
 }
 
 

@@ -53,6 +53,29 @@ struct EigArgs {
   double tol;          // rotate when |gamma| > tol * sqrt(alpha * beta)
   int use_tri;         // 1: tridiagonal eigensolve where it applies (FP32)
   double* row_mass;    // optional: sigma'^2 of each output row r (ell-1 entries)
+  // Exact Gram diagonal of a tensor-core buffer (FD_PREC_BF16X3), optional
+  // (diag64 != null enables it). The split products drop lo*lo, which on the
+  // diagonal is a sum of squares and so a bias (about 2^-19.6 of each squared
+  // norm); the diagonal is replaced by the FP64 squared norms of the rows as
+  // stored: rows 0..nret-1 (written by the previous rotate) from the rotate's
+  // per-CTA partial sums, added in a fixed order; the others from slot_n2,
+  // written at ingest.
+  int nret;
+  const double* rot_part;     // rot_nparts x rot_ld partial squared norms of rows 0..nret-1
+  int rot_nparts, rot_ld;
+  const double* slot_n2;      // FP64 squared norm of every stored new row
+  double* diag64;             // out: the exact diagonal, n entries
+  // Rayleigh-quotient refinement of the tridiagonal solve (optional, both
+  // null disables it): the loaded, scaled G is saved to gsave (n rows, row
+  // stride ldgsave, a multiple of 4) and the unscaled vectors u_0..u_ell to
+  // uvec ((ell+1) x n; at least n x ((ell+1) rounded up to 4) floats, since
+  // it then holds G U).
+  float* gsave;
+  int ldgsave;
+  float* uvec;
+  // Rows of the buffer that hold data; rows nvalid..n-1 of G are taken as
+  // zero (a flush of a partial buffer solved at the full size n). 0: all n.
+  int nvalid;
 };
 
 // t of Fast alpha-FD (Sec. 3.1): delta = sigma_t^2, t = ell - ell*alpha/2 with
@@ -69,11 +92,26 @@ cudaError_t launch_ingest(const void* src, int64_t n, int64_t ld, int dtype,
                           double* rownorm_scratch, DevCounters* ctr,
                           __nv_bfloat16* rm_hi, __nv_bfloat16* rm_lo2, int64_t ld_rm,
                           __nv_bfloat16* cm_hi, __nv_bfloat16* cm_lo, int64_t ld_cm,
-                          int row0, cudaStream_t st);
+                          int row0, cudaStream_t st, double* slot_n2 = nullptr);
+
+// Tile ingest (fd_ingest.cu): FP32 buffer rows (dst) and/or the tensor-core
+// planes, squared norms summed per tile in FP64 and added in a fixed order.
+// part: ingest_part_bytes(d, rows) bytes of scratch; ticket: a zeroed counter.
+size_t ingest_part_bytes(int64_t d, int max_rows);
+cudaError_t launch_ingest_tiles(const void* src, int64_t n, int64_t ld, int dtype, float* dst,
+                                int64_t ldd, int64_t d, int row0, __nv_bfloat16* rm_hi,
+                                __nv_bfloat16* rm_lo2, int64_t ld_rm, __nv_bfloat16* cm_hi,
+                                __nv_bfloat16* cm_lo, int64_t ld_cm, double* part,
+                                double* rownorm, double* slot_n2, DevCounters* ctr,
+                                unsigned int* ticket, int* err, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_gram_simt(const T* B, int64_t ldb, int n, int64_t d, T* parts,
                              int ldp, int ksplit, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_gram_sum_parts(const T* parts, int nparts, int ldp, int n, T* out, int ldo,
+                                  cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_eig_shrink(const EigArgs& a, cudaStream_t st);
@@ -94,6 +132,10 @@ cudaError_t launch_last_nonzero_row(const void* src, int src_f64, int64_t lds, i
                                     int* out, cudaStream_t st);
 
 cudaError_t launch_merge_counters(DevCounters* dst, const DevCounters* src, cudaStream_t st);
+
+cudaError_t launch_merge_counters_values(DevCounters* dst, const double* norm_before,
+                                         double norm_a2, double sum_delta, double removed,
+                                         long long reductions, cudaStream_t st);
 
 cudaError_t launch_compensate_rows(void* B, int b_f64, int64_t ld, int rows, int64_t d,
                                    const DevCounters* ctr, cudaStream_t st);

@@ -360,7 +360,7 @@ int na_lanczos(const TA* A, int64_t n, int d, int64_t lda, const TB* B, int64_t 
     na_normalize_kernel<<<dblocks, 256, 0, st>>>(w, c, V + (size_t)(j + 1) * NA_MAX_D, be + j, d);
     const int k = j + 1;
     const bool last = (k == kmax);
-    if (k >= 4 && ((k % 8) == 0 || last)) {
+    if ((k >= 4 && (k % 8) == 0) || last) {  // always check at the last step (d < 4 too)
       na_tri_check_kernel<<<1, 32, 0, st>>>(al, be, k, sc, res);
       e = cudaMemcpyAsync(h, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(&h_norm, na, sizeof(double), cudaMemcpyDeviceToHost, st);

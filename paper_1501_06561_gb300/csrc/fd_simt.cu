@@ -39,10 +39,11 @@ __global__ void ingest_kernel(const void* __restrict__ src, int64_t ld, int dtyp
                               double* __restrict__ rownorm, DevCounters* __restrict__ ctr,
                               __nv_bfloat16* rm_hi, __nv_bfloat16* rm_lo2, int64_t ld_rm,
                               __nv_bfloat16* cm_hi, __nv_bfloat16* cm_lo, int64_t ld_cm,
-                              int row0, int nrows) {
+                              int row0, int nrows, double* __restrict__ slot_n2) {
   const int r = blockIdx.x;
   const void* srow = src;
   double acc = 0.0;
+  float acc2 = 0.0f;  // squared norm of the stored hi + lo pair
   for (int64_t k = threadIdx.x; k < d; k += blockDim.x) {
     const double x = load_elem(srow, (int64_t)r * ld + k, dtype);
     acc += x * x;
@@ -60,15 +61,22 @@ __global__ void ingest_kernel(const void* __restrict__ src, int64_t ld, int dtyp
       rm_lo2[row * ld_rm + k] = __float2bfloat16_rn(2.0f * __bfloat162float(lo));
       cm_hi[k * ld_cm + row] = hi;
       cm_lo[k * ld_cm + row] = lo;
+      const float y = __bfloat162float(hi) + __bfloat162float(lo);
+      acc2 = fmaf(y, y, acc2);
     }
   }
-  __shared__ double red[32];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __shared__ double red[32], red2[32];
+  double a2 = (double)acc2;
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+  }
+  if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = acc; red2[threadIdx.x >> 5] = a2; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    double s = 0.0, s2 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { s += red[w]; s2 += red2[w]; }
+    if (slot_n2 != nullptr) slot_n2[row0 + r] = s2;
     rownorm[r] = s;
     __threadfence();
     const unsigned int t = atomicAdd(&ctr->ingest_ticket, 1u);
@@ -86,11 +94,11 @@ cudaError_t launch_ingest(const void* src, int64_t n, int64_t ld, int dtype, voi
                           int64_t ldd, int dst_is_f64, int64_t d, double* rownorm,
                           DevCounters* ctr, __nv_bfloat16* rm_hi, __nv_bfloat16* rm_lo2,
                           int64_t ld_rm, __nv_bfloat16* cm_hi, __nv_bfloat16* cm_lo,
-                          int64_t ld_cm, int row0, cudaStream_t st) {
+                          int64_t ld_cm, int row0, cudaStream_t st, double* slot_n2) {
   if (n <= 0) return cudaSuccess;
   ingest_kernel<<<(unsigned)n, 256, 0, st>>>(src, ld, dtype, dst, ldd, dst_is_f64, d, rownorm,
                                              ctr, rm_hi, rm_lo2, ld_rm, cm_hi, cm_lo, ld_cm,
-                                             row0, (int)n);
+                                             row0, (int)n, slot_n2);
   return cudaGetLastError();
 }
 
@@ -168,6 +176,39 @@ template cudaError_t launch_gram_simt<float>(const float*, int64_t, int, int64_t
 template cudaError_t launch_gram_simt<double>(const double*, int64_t, int, int64_t, double*,
                                               int, int, cudaStream_t);
 
+// G = (Z + Z^T) / 2 with Z the sum of the Gram's partial slices (fixed
+// order), over the whole grid, so that the one-CTA eigensolve loads a single
+// matrix (summing the slices there took longer than the solve's first phase).
+template <typename T>
+__global__ void __launch_bounds__(256) gram_sum_parts_kernel(const T* __restrict__ parts,
+                                                             int nparts, int ldp,
+                                                             int64_t part_stride, int n,
+                                                             T* __restrict__ out, int ldo) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx - (int64_t)i * n);
+  T sij = T(0), sji = T(0);
+  for (int p = 0; p < nparts; ++p) {
+    sij += parts[(int64_t)p * part_stride + (int64_t)i * ldp + j];
+    sji += parts[(int64_t)p * part_stride + (int64_t)j * ldp + i];
+  }
+  out[(int64_t)i * ldo + j] = T(0.5) * (sij + sji);
+}
+
+template <typename T>
+cudaError_t launch_gram_sum_parts(const T* parts, int nparts, int ldp, int n, T* out, int ldo,
+                                  cudaStream_t st) {
+  const int64_t tot = (int64_t)n * n;
+  gram_sum_parts_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+      parts, nparts, ldp, (int64_t)ldp * ldp, n, out, ldo);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_gram_sum_parts<float>(const float*, int, int, int, float*, int,
+                                                  cudaStream_t);
+template cudaError_t launch_gram_sum_parts<double>(const double*, int, int, int, double*, int,
+                                                   cudaStream_t);
+
 // Number of partial slices the Gram launch above produces for (d, ksplit).
 int gram_simt_slices(int64_t d, int ksplit) {
   int64_t kchunk = (d + ksplit - 1) / ksplit;
@@ -207,6 +248,7 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_shrink_kernel(EigArgs a) {
   int* rrank = ord + np;
   __shared__ int s_rot;
 
+  eig_prepare_diag(a, n);
   eig_load<T>(a, Wm, ld, n, np);
   if (tid == 0) s_rot = 0;
   __syncthreads();
@@ -296,6 +338,7 @@ __global__ void __launch_bounds__(NT) eig_fast_kernel(EigArgs a) {
   int* rrank = ord + np;
   __shared__ float s_max;
 
+  eig_prepare_diag(a, n);
   eig_load<float>(a, Wm, ld, n, np);
   if (tid == 0) s_max = 0.f;
   __syncthreads();
@@ -333,6 +376,7 @@ __global__ void __launch_bounds__(512, 1) eig_tri_kernel(EigArgs a) {
   // (tri_config checks that it is large enough), else after `small`
   unsigned char* rw = GLOBAL ? smem_raw + tri_small_bytes(n) : scr;
   __shared__ float s_max;
+  eig_prepare_diag(a, n);
   eig_load<float>(a, A, ld, n, n);
   if (tid == 0) s_max = 0.f;
   __syncthreads();
@@ -345,6 +389,13 @@ __global__ void __launch_bounds__(512, 1) eig_tri_kernel(EigArgs a) {
   const float inv = (smax > 0.f) ? 1.f / smax : 1.f;
   for (int idx = tid; idx < n * ld; idx += blockDim.x) A[idx] *= inv;
   __syncthreads();
+  if (a.gsave != nullptr) {  // the scaled G, kept for the Rayleigh quotients
+    for (int idx = tid; idx < n * a.ldgsave; idx += blockDim.x) {
+      const int i = idx / a.ldgsave, j = idx - i * a.ldgsave;
+      a.gsave[idx] = (j < n) ? A[(size_t)i * ld + j] : 0.f;
+    }
+    __syncthreads();
+  }
   tri_eig_shrink<NB, R, MAXJ, VPT>(a, A, ld, n, (smax > 0.f) ? (double)smax : 1.0, scr, small, rw);
 }
 
@@ -640,6 +691,27 @@ __global__ void merge_counters_kernel(DevCounters* dst, const DevCounters* src) 
     dst->removed += src->removed;
     dst->reductions += src->reductions;
   }
+}
+
+// fd_merge_sketch: ||A||_F^2 = its value before the rows were appended plus
+// the source stream's; the source's deltas, removed mass and reductions added.
+__global__ void merge_counters_values_kernel(DevCounters* dst, const double* norm_before,
+                                             double norm_a2, double sum_delta, double removed,
+                                             long long reductions) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    dst->norm_a2 = *norm_before + norm_a2;
+    dst->sum_delta += sum_delta;
+    dst->removed += removed;
+    dst->reductions += reductions;
+  }
+}
+
+cudaError_t launch_merge_counters_values(DevCounters* dst, const double* norm_before,
+                                         double norm_a2, double sum_delta, double removed,
+                                         long long reductions, cudaStream_t st) {
+  merge_counters_values_kernel<<<1, 32, 0, st>>>(dst, norm_before, norm_a2, sum_delta, removed,
+                                                 reductions);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_merge_counters(DevCounters* dst, const DevCounters* src, cudaStream_t st) {

@@ -41,7 +41,6 @@ cudaError_t launch_eig_shrink_f32(const EigArgs& a, cudaStream_t st);
 
 namespace {
 
-constexpr int TC_THREADS = 128;
 constexpr int TILE_BYTES = 128 * 128;  // 128 rows x 64 bf16
 constexpr long long WAIT_LIMIT = 1ll << 20;
 
@@ -172,13 +171,71 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
 }
 
 // ---------------------------------------------------------------------------
+// Accumulation. The tensor core adds the products of one MMA into its FP32
+// accumulator with truncation, so a long chain of MMAs into one accumulator
+// drifts toward zero by about half an ulp per MMA; over the thousands of
+// reductions of a stream that bias removes mass from every retained row.
+// Each K = 16 step therefore goes into a fresh TMEM accumulator (two,
+// alternating), and four epilogue warps add it into a running sum held in
+// registers with FP32 round-to-nearest adds while the next step runs.
+// Warp roles: 0 = TMA producer, 1 = MMA issuer (and TMEM owner), 2..5 =
+// epilogue (warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31).
+// ---------------------------------------------------------------------------
+constexpr int TC_WARPS = 6;
+constexpr int TC_NT = 32 * TC_WARPS;
+constexpr uint32_t TC_TMEM_COLS = 256;  // two accumulators of up to 128 columns
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait of every lane of a warp; true only if all lanes saw the phase.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, int* err) {
+  const bool ok = mbar_wait(bar, parity, err);
+  return __all_sync(0xffffffffu, ok) != 0;
+}
+
+// Epilogue: drain accumulator b (columns b*128 .. b*128 + 32*nch - 1 of this
+// warp's 32 lanes) into acc with round-to-nearest adds.
+template <int NCH>
+__device__ __forceinline__ void drain_add(uint32_t taddr, int q, int b, int nch, float* acc) {
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    if (c < nch) {
+      float v[32];
+      tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 128 + c * 32), v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) acc[c * 32 + i] += v[i];
+    }
+  }
+}
+
+// The same for two accumulators per step: the large products (columns
+// b*128..) and the small cross products (columns 256 + b*128..).
+template <int NCH>
+__device__ __forceinline__ void drain_add2(uint32_t taddr, int q, int b, int nch, float* acc) {
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    if (c < nch) {
+      float v[32], w[32];
+      tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 128 + c * 32), v);
+      tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(256 + b * 128 + c * 32), w);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) acc[c * 32 + i] += v[i] + w[i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Gram kernel. Grid = tiles * ks (cluster of ks CTAs along x per 128x128 tile).
+// Each CTA sums its share of K; the ks partial tiles are added in a fixed
+// order through distributed shared memory.
 // ---------------------------------------------------------------------------
 constexpr int GRAM_STAGES = 4;
 constexpr int GRAM_STAGE_BYTES = 3 * TILE_BYTES;  // A (hi), B (hi), B (2 lo)
 constexpr int GRAM_PLD = 129;                     // partial tile row stride (floats)
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_NT, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap map_hi,
                    const __grid_constant__ CUtensorMap map_lo2, float* __restrict__ G, int ldg,
                    int nrows, int kblocks, int ks, int ntiles_side, int* err) {
@@ -187,8 +244,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint8_t* stages = smem;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + GRAM_STAGES * GRAM_STAGE_BYTES);
   uint64_t* empty = full + GRAM_STAGES;
-  uint64_t* done = empty + GRAM_STAGES;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* accfull = empty + GRAM_STAGES;
+  uint64_t* accfree = accfull + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accfree + 2);
   float* part = reinterpret_cast<float*>(stages);  // reused after the MMAs complete
 
   cg::cluster_group cluster = cg::this_cluster();
@@ -199,22 +257,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int per = (kblocks + ks - 1) / ks;
   const int kb0 = min(kblocks, rank * per), kb1 = min(kblocks, kb0 + per);
   const int nk = kb1 - kb0;
+  const int nsteps = 4 * nk;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < GRAM_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) { mbar_init(&accfull[b], 1); mbar_init(&accfree[b], 4); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 2) tmem_alloc(tslot, 128);
+  if (warp == 1) tmem_alloc(tslot, TC_TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = *tslot;
-  bool ok = true;
 
-  if (nk > 0) {
-    if (warp == 0 && lane == 0) {
+  if (warp == 0) {
+    if (lane == 0) {
+      bool ok = true;
       for (int it = 0; it < nk && ok; ++it) {
         const int s = it % GRAM_STAGES;
         if (it >= GRAM_STAGES) ok = mbar_wait(&empty[s], ((it / GRAM_STAGES) - 1) & 1, err);
@@ -226,53 +285,62 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tma_load_2d(st + TILE_BYTES, &map_hi, &full[s], kc, j0);
         tma_load_2d(st + 2 * TILE_BYTES, &map_lo2, &full[s], kc, j0);
       }
-    } else if (warp == 1 && lane == 0) {
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
       const uint32_t idesc = idesc_bf16(128, 128);
+      bool ok = true;
       for (int it = 0; it < nk && ok; ++it) {
         const int s = it % GRAM_STAGES;
         ok = mbar_wait(&full[s], (it / GRAM_STAGES) & 1, err);
         if (!ok) break;
         tc_fence_after();
         uint8_t* st = stages + s * GRAM_STAGE_BYTES;
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll 1
+        for (int kk = 0; kk < 4 && ok; ++kk) {
+          const int step = it * 4 + kk, b = step & 1;
+          if (step >= 2) {
+            ok = mbar_wait(&accfree[b], ((step >> 1) - 1) & 1, err);
+            if (!ok) break;
+            tc_fence_after();
+          }
+          const uint32_t dt = taddr + (uint32_t)(b * 128);
           const uint64_t a = smem_desc_sw128(st + kk * 32);
           const uint64_t b1 = smem_desc_sw128(st + TILE_BYTES + kk * 32);
           const uint64_t b2 = smem_desc_sw128(st + 2 * TILE_BYTES + kk * 32);
-          mma_bf16(taddr, a, b1, idesc, (it > 0 || kk > 0) ? 1u : 0u);
-          mma_bf16(taddr, a, b2, idesc, 1u);
+          mma_bf16(dt, a, b1, idesc, 0u);
+          mma_bf16(dt, a, b2, idesc, 1u);
+          mma_commit(&accfull[b]);
         }
         mma_commit(&empty[s]);
       }
-      mma_commit(done);
     }
-    __syncwarp();
-    // every thread waits for the accumulator (bounded)
-    if (!mbar_wait(done, 0, err)) ok = false;
-    tc_fence_after();
-  }
-  // accumulator -> shared partial tile (row = TMEM lane)
-  {
-    const int r = warp * 32 + lane;
-    float v[32];
-    for (int c = 0; c < 4; ++c) {
-      if (nk > 0 && ok) {
-        tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
-      } else {
+  } else {
+    // epilogue: running sum of row r = 32 q + lane over the 128 columns
+    const int q = warp & 3, r = q * 32 + lane;
+    float acc[128];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = 0.0f;
-      }
-#pragma unroll
-      for (int i = 0; i < 32; ++i) part[r * GRAM_PLD + c * 32 + i] = v[i];
+    for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
+    for (int step = 0; step < nsteps; ++step) {
+      const int b = step & 1;
+      if (!warp_wait(&accfull[b], (step >> 1) & 1, err)) break;
+      tc_fence_after();
+      drain_add<4>(taddr, q, b, 4, acc);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&accfree[b]);
     }
+#pragma unroll
+    for (int i = 0; i < 128; ++i) part[r * GRAM_PLD + i] = acc[i];
   }
+  __syncwarp();  // the producer and MMA lanes rejoin their warps
   tc_fence_before();
   cluster.sync();
   // fixed-order sum of the ks partial tiles; this CTA writes its row slice
   {
     const int rows_per = (128 + ks - 1) / ks;
     const int rs0 = rank * rows_per, rs1 = min(128, rs0 + rows_per);
-    for (int idx = threadIdx.x; idx < (rs1 - rs0) * 128; idx += TC_THREADS) {
+    for (int idx = threadIdx.x; idx < (rs1 - rs0) * 128; idx += TC_NT) {
       const int r = rs0 + idx / 128, c = idx % 128;
       float s = 0.0f;
       for (int q = 0; q < ks; ++q) {
@@ -285,118 +353,184 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   cluster.sync();
   tc_fence_after();
-  if (warp == 2) tmem_dealloc(taddr, 128);
+  if (warp == 1) tmem_dealloc(taddr, TC_TMEM_COLS);
 }
 
 // ---------------------------------------------------------------------------
-// Rotate kernel. Grid = ceil(d / 128). N = Np (ell-1 padded to 16).
+// Rotate kernel. Grid = (ceil(d / 128), nsplit): CTA (x, y) computes the
+// 128 values m0 .. m0+127 of d for output rows y*NC .. y*NC + NC - 1
+// (NC <= 128, a multiple of 16; nsplit * NC >= ell - 1). The hi*hi products
+// of a step have an accumulator of their own (the truncation of one MMA is
+// relative to its result, and the retained row's own term makes that result
+// as large as the output); the small cross products share a second one.
 // ---------------------------------------------------------------------------
 constexpr int ROT_STAGES = 2;
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_NT, 1)
     rotate_tc_kernel(const __grid_constant__ CUtensorMap map_cm_hi,
                      const __grid_constant__ CUtensorMap map_cm_lo,
                      const __grid_constant__ CUtensorMap map_w_hi,
-                     const __grid_constant__ CUtensorMap map_w_lo, int kblocks, int Np, int nout,
+                     const __grid_constant__ CUtensorMap map_w_lo, int kblocks, int NC, int nout,
                      int64_t d, __nv_bfloat16* rm_hi, __nv_bfloat16* rm_lo2, int64_t ld_rm,
                      __nv_bfloat16* cm_hi, __nv_bfloat16* cm_lo, int64_t ld_cm,
-                     float* out_rows, int64_t ldo, int* err) {
+                     float* out_rows, int64_t ldo, double* rot_part, int rot_ld, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
-  const int wbytes = Np * 128;
+  const int wbytes = NC * 128;
   const int stage_bytes = 2 * TILE_BYTES + 2 * wbytes;
   uint8_t* stages = smem;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + ROT_STAGES * stage_bytes);
   uint64_t* empty = full + ROT_STAGES;
-  uint64_t* done = empty + ROT_STAGES;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* accfull = empty + ROT_STAGES;
+  uint64_t* accfree = accfull + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accfree + 2);
   const int m0 = blockIdx.x * 128;
+  const int n0 = blockIdx.y * NC;
+  const int nsteps = 4 * kblocks;
+  const int nch = (NC + 31) / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t tcols = 256;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ROT_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) { mbar_init(&accfull[b], 1); mbar_init(&accfree[b], 4); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 2) tmem_alloc(tslot, tcols);
+  if (warp == 1) tmem_alloc(tslot, 2 * TC_TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = *tslot;
-  bool ok = true;
 
-  if (warp == 0 && lane == 0) {
-    for (int it = 0; it < kblocks && ok; ++it) {
-      const int s = it % ROT_STAGES;
-      if (it >= ROT_STAGES) ok = mbar_wait(&empty[s], ((it / ROT_STAGES) - 1) & 1, err);
-      if (!ok) break;
-      uint8_t* st = stages + s * stage_bytes;
-      mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
-      const int kc = it * 64;
-      tma_load_2d(st, &map_cm_hi, &full[s], kc, m0);
-      tma_load_2d(st + TILE_BYTES, &map_cm_lo, &full[s], kc, m0);
-      tma_load_2d(st + 2 * TILE_BYTES, &map_w_hi, &full[s], kc, 0);
-      tma_load_2d(st + 2 * TILE_BYTES + wbytes, &map_w_lo, &full[s], kc, 0);
+  float acc[128];
+#pragma unroll
+  for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
+  bool drained = true;
+  if (warp == 0) {
+    if (lane == 0) {
+      bool ok = true;
+      for (int it = 0; it < kblocks && ok; ++it) {
+        const int s = it % ROT_STAGES;
+        if (it >= ROT_STAGES) ok = mbar_wait(&empty[s], ((it / ROT_STAGES) - 1) & 1, err);
+        if (!ok) break;
+        uint8_t* st = stages + s * stage_bytes;
+        mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
+        const int kc = it * 64;
+        tma_load_2d(st, &map_cm_hi, &full[s], kc, m0);
+        tma_load_2d(st + TILE_BYTES, &map_cm_lo, &full[s], kc, m0);
+        tma_load_2d(st + 2 * TILE_BYTES, &map_w_hi, &full[s], kc, n0);
+        tma_load_2d(st + 2 * TILE_BYTES + wbytes, &map_w_lo, &full[s], kc, n0);
+      }
     }
-  } else if (warp == 1 && lane == 0) {
-    const uint32_t idesc = idesc_bf16(128, Np);
-    for (int it = 0; it < kblocks && ok; ++it) {
-      const int s = it % ROT_STAGES;
-      ok = mbar_wait(&full[s], (it / ROT_STAGES) & 1, err);
-      if (!ok) break;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, NC);
+      bool ok = true;
+      for (int it = 0; it < kblocks && ok; ++it) {
+        const int s = it % ROT_STAGES;
+        ok = mbar_wait(&full[s], (it / ROT_STAGES) & 1, err);
+        if (!ok) break;
+        tc_fence_after();
+        uint8_t* st = stages + s * stage_bytes;
+#pragma unroll 1
+        for (int kk = 0; kk < 4 && ok; ++kk) {
+          const int step = it * 4 + kk, b = step & 1;
+          if (step >= 2) {
+            ok = mbar_wait(&accfree[b], ((step >> 1) - 1) & 1, err);
+            if (!ok) break;
+            tc_fence_after();
+          }
+          const uint32_t dt = taddr + (uint32_t)(b * 128);
+          const uint32_t dx = taddr + (uint32_t)(256 + b * 128);
+          const uint64_t ah = smem_desc_sw128(st + kk * 32);
+          const uint64_t al = smem_desc_sw128(st + TILE_BYTES + kk * 32);
+          const uint64_t wh = smem_desc_sw128(st + 2 * TILE_BYTES + kk * 32);
+          const uint64_t wl = smem_desc_sw128(st + 2 * TILE_BYTES + wbytes + kk * 32);
+          mma_bf16(dt, ah, wh, idesc, 0u);
+          mma_bf16(dx, ah, wl, idesc, 0u);
+          mma_bf16(dx, al, wh, idesc, 1u);
+          mma_commit(&accfull[b]);
+        }
+        mma_commit(&empty[s]);
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    for (int step = 0; step < nsteps; ++step) {
+      const int b = step & 1;
+      if (!warp_wait(&accfull[b], (step >> 1) & 1, err)) { drained = false; break; }
       tc_fence_after();
-      uint8_t* st = stages + s * stage_bytes;
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint64_t ah = smem_desc_sw128(st + kk * 32);
-        const uint64_t al = smem_desc_sw128(st + TILE_BYTES + kk * 32);
-        const uint64_t wh = smem_desc_sw128(st + 2 * TILE_BYTES + kk * 32);
-        const uint64_t wl = smem_desc_sw128(st + 2 * TILE_BYTES + wbytes + kk * 32);
-        mma_bf16(taddr, ah, wh, idesc, (it > 0 || kk > 0) ? 1u : 0u);
-        mma_bf16(taddr, ah, wl, idesc, 1u);
-        mma_bf16(taddr, al, wh, idesc, 1u);
-      }
-      mma_commit(&empty[s]);
+      drain_add2<4>(taddr, q, b, nch, acc);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&accfree[b]);
     }
-    mma_commit(done);
   }
-  __syncwarp();
-  if (!mbar_wait(done, 0, err)) ok = false;
+  // Every MMA has completed and every stage was consumed once the epilogue
+  // saw the last step, so the stage memory is free for the row sums.
+  __syncwarp();  // the producer and MMA lanes rejoin their warps
+  tc_fence_before();
+  __syncthreads();
   tc_fence_after();
-
-  const int64_t m = m0 + warp * 32 + lane;  // this thread's d index
-  const int nchunks = (Np + 31) / 32;
-  for (int c = 0; c < nchunks; ++c) {
-    float v[32];
-    if (ok) {
-      tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
-    } else {
+  float* wsum = reinterpret_cast<float*>(stages);  // 4 x 128 partial squared norms
+  if (warp >= 2) {
+    const int q = warp & 3;
+    const int64_t m = m0 + q * 32 + lane;  // this thread's d index
+    const bool live = (m < d) && drained;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = 0.0f;
-    }
-    if (m >= d || !ok) continue;
-#pragma unroll 4
-    for (int i = 0; i < 32; ++i) {
-      const int j = c * 32 + i;
-      if (j >= nout) break;
-      const float x = v[i];
-      if (out_rows) {
-        out_rows[(int64_t)j * ldo + m] = x;
-      } else {
-        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-        cm_hi[m * ld_cm + j] = hi;
-        cm_lo[m * ld_cm + j] = lo;
-        rm_hi[(int64_t)j * ld_rm + m] = hi;
-        rm_lo2[(int64_t)j * ld_rm + m] = __float2bfloat16_rn(2.0f * __bfloat162float(lo));
+    for (int c = 0; c < 4; ++c) {
+      if (c >= nch) break;  // warp-uniform
+      float v[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int jl = c * 32 + i, j = n0 + jl;
+        const float x = acc[c * 32 + i];
+        float sq = 0.0f;
+        if (live && jl < NC && j < nout) {
+          if (out_rows) {
+            out_rows[(int64_t)j * ldo + m] = x;
+          } else {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+            cm_hi[m * ld_cm + j] = hi;
+            cm_lo[m * ld_cm + j] = lo;
+            rm_hi[(int64_t)j * ld_rm + m] = hi;
+            rm_lo2[(int64_t)j * ld_rm + m] = __float2bfloat16_rn(2.0f * __bfloat162float(lo));
+            const float y = __bfloat162float(hi) + __bfloat162float(lo);
+            sq = y * y;
+          }
+        }
+        v[i] = sq;
       }
+      if (rot_part != nullptr) {
+        // transpose-reduce: after the step with offset o each lane keeps the
+        // half of its values selected by its bit o, added to its partner's;
+        // lane i ends with row c*32+i summed over the warp's 32 columns
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+          const bool up = (lane & o) != 0;
+#pragma unroll
+          for (int k = 0; k < o; ++k) {
+            const float send = up ? v[k] : v[k + o];
+            const float keep = up ? v[k + o] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+          }
+        }
+        wsum[q * 128 + c * 32 + lane] = v[0];
+      }
+    }
+  }
+  if (rot_part != nullptr) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < NC; j += TC_NT) {
+      const double t = ((double)wsum[j] + (double)wsum[128 + j]) +
+                       ((double)wsum[256 + j] + (double)wsum[384 + j]);
+      rot_part[(int64_t)blockIdx.x * rot_ld + n0 + j] = t;
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 2) tmem_dealloc(taddr, tcols);
+  if (warp == 1) tmem_dealloc(taddr, 2 * TC_TMEM_COLS);
 }
 
 // hi + lo of the first `rows` buffer rows as FP32 (row-major planes).
@@ -449,13 +583,23 @@ bool make_map(CUtensorMap* map, void* base, uint64_t ld, uint64_t rows, uint32_t
 
 struct TcCtx {
   int64_t d = 0, ldb = 0;
-  int ell = 0, L = 0, ldl = 0, Np = 0;
+  int ell = 0, L = 0, ldl = 0;
+  int NC = 0, nsplit = 1;  // rotate output rows per CTA, CTAs along them
   cudaStream_t st = nullptr;
   __nv_bfloat16 *rm_hi = nullptr, *rm_lo2 = nullptr, *cm_hi = nullptr, *cm_lo = nullptr;
   __nv_bfloat16 *w_hi = nullptr, *w_lo = nullptr;
   float* G = nullptr;
   float* wrot32 = nullptr;
   int* err = nullptr;
+  // exact Gram diagonal (see EigArgs): FP64 squared norms of the stored new
+  // rows, the rotate's per-CTA partial squared norms of the rows it wrote,
+  // and the per-reduction diagonal
+  double* slot_n2 = nullptr;
+  double* rot_part = nullptr;
+  double* diag64 = nullptr;
+  int rot_grid = 0, rot_ld = 0;
+  int keep = 0;   // rows a reduction leaves
+  int nret = 0;   // leading buffer rows written by the last committed rotate
   CUtensorMap m_rm_hi, m_rm_lo2, m_cm_hi, m_cm_lo, m_w_hi, m_w_lo;
   int ks = 1;
   size_t gram_smem = 0, rot_smem = 0;
@@ -467,10 +611,11 @@ void tc_destroy(TcCtx* t) {
   if (!t) return;
   cudaFree(t->rm_hi); cudaFree(t->rm_lo2); cudaFree(t->cm_hi); cudaFree(t->cm_lo);
   cudaFree(t->w_hi); cudaFree(t->w_lo); cudaFree(t->G); cudaFree(t->wrot32); cudaFree(t->err);
+  cudaFree(t->slot_n2); cudaFree(t->rot_part); cudaFree(t->diag64);
   delete t;
 }
 
-int tc_create(TcCtx** out, int64_t d, int ell, int L, cudaStream_t st) {
+int tc_create(TcCtx** out, int64_t d, int ell, int L, int keep, cudaStream_t st) {
   *out = nullptr;
   TcCtx* t = new (std::nothrow) TcCtx();
   if (!t) return FD_ENOMEM;
@@ -479,12 +624,19 @@ int tc_create(TcCtx** out, int64_t d, int ell, int L, cudaStream_t st) {
   t->ell = ell;
   t->L = L;
   t->ldl = (t->L + 63) / 64 * 64;
-  t->Np = ((ell - 1) + 15) / 16 * 16;
-  if (t->Np < 16) t->Np = 16;
+  {
+    int np = ((ell - 1) + 15) / 16 * 16;
+    if (np < 16) np = 16;
+    t->nsplit = (np + 127) / 128;
+    t->NC = ((np + t->nsplit - 1) / t->nsplit + 15) / 16 * 16;
+  }
+  t->rot_ld = t->nsplit * t->NC;
   t->st = st;
+  t->keep = keep;
+  t->rot_grid = (int)((d + 127) / 128);
   const size_t plane_rm = (size_t)t->L * t->ldb * 2;
   const size_t plane_cm = (size_t)t->ldb * t->ldl * 2;
-  const size_t wplane = (size_t)t->Np * t->ldl * 2;
+  const size_t wplane = (size_t)t->rot_ld * t->ldl * 2;
   cudaError_t e = cudaSuccess;
   auto alloc = [&](void** p, size_t b) {
     if (e != cudaSuccess) return;
@@ -500,6 +652,9 @@ int tc_create(TcCtx** out, int64_t d, int ell, int L, cudaStream_t st) {
   alloc((void**)&t->G, (size_t)t->L * t->L * 4);
   alloc((void**)&t->wrot32, (size_t)ell * t->ldl * 4);
   alloc((void**)&t->err, sizeof(int));
+  alloc((void**)&t->slot_n2, (size_t)t->L * 8);
+  alloc((void**)&t->rot_part, (size_t)t->rot_grid * t->rot_ld * 8);
+  alloc((void**)&t->diag64, (size_t)t->L * 8);
   if (e != cudaSuccess) {
     set_cuda_error(e, "tc_create alloc");
     tc_destroy(t);
@@ -509,8 +664,8 @@ int tc_create(TcCtx** out, int64_t d, int ell, int L, cudaStream_t st) {
             make_map(&t->m_rm_lo2, t->rm_lo2, t->ldb, t->L, 128) &&
             make_map(&t->m_cm_hi, t->cm_hi, t->ldl, t->ldb, 128) &&
             make_map(&t->m_cm_lo, t->cm_lo, t->ldl, t->ldb, 128) &&
-            make_map(&t->m_w_hi, t->w_hi, t->ldl, t->Np, t->Np) &&
-            make_map(&t->m_w_lo, t->w_lo, t->ldl, t->Np, t->Np);
+            make_map(&t->m_w_hi, t->w_hi, t->ldl, t->rot_ld, t->NC) &&
+            make_map(&t->m_w_lo, t->w_lo, t->ldl, t->rot_ld, t->NC);
   if (!ok) {
     tc_destroy(t);
     return FD_EINVAL;
@@ -519,7 +674,7 @@ int tc_create(TcCtx** out, int64_t d, int ell, int L, cudaStream_t st) {
   t->ks = kblocks < 8 ? kblocks : 8;
   if (t->ks < 1) t->ks = 1;
   t->gram_smem = 1024 + GRAM_STAGES * GRAM_STAGE_BYTES + 256;
-  t->rot_smem = 1024 + ROT_STAGES * (2 * TILE_BYTES + 2 * t->Np * 128) + 256;
+  t->rot_smem = 1024 + ROT_STAGES * (2 * TILE_BYTES + 2 * t->NC * 128) + 256;
   e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)t->gram_smem);
   if (e == cudaSuccess)
@@ -535,9 +690,11 @@ int tc_create(TcCtx** out, int64_t d, int ell, int L, cudaStream_t st) {
 }
 
 int tc_ingest(TcCtx* t, const void* src, int64_t n, int64_t ld, int dtype, int row0,
-              double* rownorm, DevCounters* ctr) {
-  cudaError_t e = launch_ingest(src, n, ld, dtype, nullptr, 0, 0, t->d, rownorm, ctr, t->rm_hi,
-                                t->rm_lo2, t->ldb, t->cm_hi, t->cm_lo, t->ldl, row0, t->st);
+              double* rownorm, DevCounters* ctr, double* part) {
+  cudaError_t e = launch_ingest_tiles(src, n, ld, dtype, nullptr, 0, t->d, row0, t->rm_hi,
+                                      t->rm_lo2, t->ldb, t->cm_hi, t->cm_lo, t->ldl, part,
+                                      rownorm, t->slot_n2, ctr, &ctr->ingest_ticket, t->err,
+                                      t->st);
   if (e != cudaSuccess) { set_cuda_error(e, "tc_ingest"); return FD_ECUDA; }
   return FD_OK;
 }
@@ -569,7 +726,7 @@ int tc_gram(TcCtx* t, int nrows) {
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3((unsigned)(side * side * t->ks), 1, 1);
-  cfg.blockDim = dim3(TC_THREADS, 1, 1);
+  cfg.blockDim = dim3(TC_NT, 1, 1);
   cfg.dynamicSmemBytes = t->gram_smem;
   cfg.stream = t->st;
   cfg.attrs = attr;
@@ -580,9 +737,16 @@ int tc_gram(TcCtx* t, int nrows) {
   return FD_OK;
 }
 
-int tc_eig(TcCtx* t, const EigArgs& tmpl) {
+int tc_eig(TcCtx* t, const EigArgs& tmpl, int commit) {
   cudaError_t e;
   EigArgs a = tmpl;
+  a.nret = t->nret;
+  a.rot_part = t->rot_part;
+  a.rot_nparts = t->rot_grid;
+  a.rot_ld = t->rot_ld;
+  a.slot_n2 = t->slot_n2;
+  a.diag64 = t->diag64;
+  (void)commit;
   a.parts = t->G;
   a.nparts = 1;
   a.ldp = t->L;
@@ -601,13 +765,14 @@ int tc_eig(TcCtx* t, const EigArgs& tmpl) {
 int tc_rotate(TcCtx* t, int nrows, int write_sketch, float* sketch_out, int64_t ldo) {
   cudaError_t e;
   const int kb_rot = (nrows + 63) / 64;
-  const unsigned grid = (unsigned)((t->d + 127) / 128);
-  rotate_tc_kernel<<<grid, TC_THREADS, t->rot_smem, t->st>>>(
-      t->m_cm_hi, t->m_cm_lo, t->m_w_hi, t->m_w_lo, kb_rot, t->Np, t->ell - 1, t->d, t->rm_hi,
+  const dim3 grid((unsigned)t->rot_grid, (unsigned)t->nsplit, 1);
+  rotate_tc_kernel<<<grid, TC_NT, t->rot_smem, t->st>>>(
+      t->m_cm_hi, t->m_cm_lo, t->m_w_hi, t->m_w_lo, kb_rot, t->NC, t->ell - 1, t->d, t->rm_hi,
       t->rm_lo2, t->ldb, t->cm_hi, t->cm_lo, t->ldl, write_sketch ? sketch_out : nullptr, ldo,
-      t->err);
+      write_sketch ? nullptr : t->rot_part, t->rot_ld, t->err);
   e = cudaGetLastError();
   if (e != cudaSuccess) { set_cuda_error(e, "rotate_tc_kernel"); return FD_ECUDA; }
+  if (!write_sketch) t->nret = t->keep;
   return FD_OK;
 }
 
@@ -621,6 +786,7 @@ int tc_reset(TcCtx* t) {
   if (e == cudaSuccess) e = cudaMemsetAsync(t->cm_lo, 0, plane_cm, t->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->err, 0, sizeof(int), t->st);
   if (e != cudaSuccess) { set_cuda_error(e, "tc_reset"); return FD_ECUDA; }
+  t->nret = 0;
   return FD_OK;
 }
 

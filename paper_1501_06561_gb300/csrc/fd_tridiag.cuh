@@ -56,10 +56,13 @@ __host__ __device__ constexpr int tri_ldz(int count) { return count | 1; }
 __host__ __device__ constexpr size_t tri_scratch_bytes(int n, int NB) {
   // max of: LU bands + pivots (NB vectors); Cholesky matrix + inverse diagonal
   // (count <= n/2) and the Sturm counts of the grid pass (<= 1024 threads)
+  // (count <= n/2 + 1: the retained vectors and the one at the cut)
   return (tri_al16((size_t)NB * n * 16) + tri_al16((size_t)NB * n)) >
-                 tri_al16((size_t)(n / 2) * ((n / 2) | 1) * 4) + tri_al16((size_t)(n / 2) * 4) + 4096
+                 tri_al16((size_t)(n / 2 + 1) * ((n / 2 + 1) | 1) * 4) +
+                     tri_al16((size_t)(n / 2 + 1) * 4) + 4096
              ? tri_al16((size_t)NB * n * 16) + tri_al16((size_t)NB * n)
-             : tri_al16((size_t)(n / 2) * ((n / 2) | 1) * 4) + tri_al16((size_t)(n / 2) * 4) + 4096;
+             : tri_al16((size_t)(n / 2 + 1) * ((n / 2 + 1) | 1) * 4) +
+                   tri_al16((size_t)(n / 2 + 1) * 4) + 4096;
 }
 // floats of the small-vector region: red (64), five vectors of 8*ceil(n/8)
 // (xb, vb0, vb1, qb, pb), d, e, e2, lam (n each)
@@ -380,9 +383,14 @@ static __device__ void tri_reduce(float* A, int ld, int n, float* d, float* e, u
 }
 
 // Number of eigenvalues of T below x (signs of the LDL^T pivots of T - x I).
+// A pivot smaller than pivmin in magnitude is replaced by -pivmin before its
+// sign is counted, so that the count and the rest of the recurrence see the
+// same pivot (counting a zero pivot as non-negative while dividing by
+// -pivmin made the count drop by one where x equals a diagonal entry).
 __device__ __forceinline__ int tri_sturm(const float* d, const float* e2, int n, float x,
                                          float pivmin) {
   float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
   int cnt = (q < 0.f);
   int i = 1;
   for (; i + 7 < n; i += 8) {  // loads of a chunk first, then the pivot chain
@@ -394,14 +402,14 @@ __device__ __forceinline__ int tri_sturm(const float* d, const float* e2, int n,
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      if (fabsf(q) < pivmin) q = -pivmin;
       q = dx[u] - __fdividef(ee[u], q);
+      if (fabsf(q) < pivmin) q = -pivmin;
       cnt += (q < 0.f);
     }
   }
   for (; i < n; ++i) {
-    if (fabsf(q) < pivmin) q = -pivmin;
     q = (d[i] - x) - __fdividef(e2[i - 1], q);
+    if (fabsf(q) < pivmin) q = -pivmin;
     cnt += (q < 0.f);
   }
   return cnt;
@@ -960,6 +968,146 @@ __device__ __forceinline__ float tri_block_sum(float v, float* red) {
   return s;
 }
 
+// Fallback of step 4 for eigenvalues that bisection cannot tell apart.
+// Columns are taken in order of their position in the spectrum; a group is a
+// run of consecutive ones whose eigenvalues differ by at most gt. The group's
+// first column keeps its twisted vector, the others start from pseudo-random
+// vectors; then two rounds of block inverse iteration: every member takes one
+// solve of (T - lambda I) z = z (LU with partial pivoting, one thread per
+// member, NB at a time), and each group is made orthonormal again by two
+// passes of classical Gram-Schmidt in its order. The group's columns then span
+// its invariant subspace instead of repeating one vector.
+// scr: NB x 3n floats; ord, gstart, mlist: count ints each; hbuf: count
+// floats; red: block-sum scratch.
+template <int NB>
+__device__ void tri_tight_repair(float* Zt, int ldz, int n, const float* d, const float* e,
+                                 const float* lam, const int* pos, int count, float gt,
+                                 float tnorm, float* scr, int* ord, int* gstart, int* mlist,
+                                 float* hbuf, float* red, int* s_ng) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int r = tid; r < count; r += nt) {
+    const int pr = pos[r];
+    int rank = 0;
+    for (int q = 0; q < count; ++q) rank += (pos[q] < pr);
+    ord[rank] = r;
+  }
+  __syncthreads();
+  __shared__ int s_nm;
+  if (tid == 0) {
+    int ng = 0, nm = 0;
+    for (int a = 0; a < count;) {
+      int b = a + 1;
+      while (b < count && lam[pos[ord[b - 1]]] - lam[pos[ord[b]]] <= gt) ++b;
+      if (b - a >= 2) {
+        gstart[2 * ng] = a;
+        gstart[2 * ng + 1] = b;
+        ++ng;
+        for (int m = a; m < b; ++m) mlist[nm++] = ord[m];
+      }
+      a = b;
+    }
+    *s_ng = ng;
+    s_nm = nm;
+  }
+  __syncthreads();
+  const int ng = *s_ng, nm = s_nm;
+  // pseudo-random starts for all but each group's first member
+  for (int g = 0; g < ng; ++g) {
+    const int a = gstart[2 * g], b = gstart[2 * g + 1];
+    for (int idx = tid; idx < (b - a - 1) * n; idx += nt) {
+      const int c = ord[a + 1 + idx / n], i = idx % n;
+      unsigned h = (unsigned)(i * 2654435761u) ^ (unsigned)(c * 40503u + 0x7f4a7c15u);
+      h ^= h >> 15; h *= 2246822519u; h ^= h >> 13;
+      Zt[(size_t)i * ldz + c] = (float)(h & 0xffff) / 65536.f - 0.5f;
+    }
+  }
+  __syncthreads();
+  const float eps = 1.1920929e-07f;
+  const float tiny = eps * fmaxf(tnorm, 1e-30f);
+  for (int round = 0; round < 2; ++round) {
+    for (int c0 = 0; c0 < nm; c0 += NB) {
+      const int t = tid;
+      if (t < NB && c0 + t < nm) {
+        const int c = mlist[c0 + t];
+        float* z = Zt + c;
+        float* ru = scr;
+        float* du = scr + (size_t)NB * n;
+        float* du2 = scr + (size_t)2 * NB * n;
+#define RU(i) ru[(size_t)(i) * NB + t]
+#define DU(i) du[(size_t)(i) * NB + t]
+#define DU2(i) du2[(size_t)(i) * NB + t]
+        const float lmb = lam[pos[c]];
+        float dc = d[0] - lmb, uc = (n > 1) ? e[0] : 0.f, u2c = 0.f, zc = z[0];
+        for (int i = 0; i + 1 < n; ++i) {
+          const float li = e[i];
+          const float dn = d[i + 1] - lmb, un = (i + 2 < n) ? e[i + 1] : 0.f;
+          const float zn = z[(size_t)(i + 1) * ldz];
+          if (fabsf(dc) >= fabsf(li)) {
+            const float dv = (dc == 0.f) ? tiny : dc;
+            const float f = __fdividef(li, dv);
+            RU(i) = __fdividef(1.f, dv); DU(i) = uc; DU2(i) = u2c; z[(size_t)i * ldz] = zc;
+            dc = fmaf(-f, uc, dn); uc = fmaf(-f, u2c, un); zc = fmaf(-f, zc, zn);
+          } else {
+            const float f = __fdividef(dc, li);
+            RU(i) = __fdividef(1.f, li); DU(i) = dn; DU2(i) = un; z[(size_t)i * ldz] = zn;
+            dc = fmaf(-f, dn, uc); uc = fmaf(-f, un, u2c); zc = fmaf(-f, zn, zc);
+          }
+          u2c = 0.f;
+        }
+        float x = zc * __fdividef(1.f, (dc == 0.f) ? tiny : dc), x2 = 0.f, mx = fabsf(x);
+        z[(size_t)(n - 1) * ldz] = x;
+        for (int i = n - 2; i >= 0; --i) {
+          const float v = fmaf(-DU2(i), x2, fmaf(-DU(i), x, z[(size_t)i * ldz])) * RU(i);
+          z[(size_t)i * ldz] = v;
+          x2 = x; x = v;
+          mx = fmaxf(mx, fabsf(v));
+        }
+        const float inv = (mx > 0.f) ? 1.f / mx : 1.f;
+        for (int i = 0; i < n; ++i) z[(size_t)i * ldz] *= inv;
+#undef RU
+#undef DU
+#undef DU2
+      }
+      __syncthreads();
+    }
+    // each group orthonormal again, in its order (CGS, two passes)
+    for (int g = 0; g < ng; ++g) {
+      const int a = gstart[2 * g], b = gstart[2 * g + 1];
+      for (int m = a; m < b; ++m) {
+        const int c = ord[m];
+        for (int pass = 0; pass < 2 && m > a; ++pass) {
+          for (int q = a + warp; q < m; q += nw) {
+            const int cp = ord[q];
+            float sdot = 0.f;
+            for (int i = lane; i < n; i += 32)
+              sdot = fmaf(Zt[(size_t)i * ldz + cp], Zt[(size_t)i * ldz + c], sdot);
+            sdot = warp_sum(sdot);
+            if (lane == 0) hbuf[q - a] = sdot;
+          }
+          __syncthreads();
+          for (int i = tid; i < n; i += nt) {
+            float sacc = 0.f;
+            for (int q = a; q < m; ++q) sacc = fmaf(hbuf[q - a], Zt[(size_t)i * ldz + ord[q]], sacc);
+            Zt[(size_t)i * ldz + c] -= sacc;
+          }
+          __syncthreads();
+        }
+        float s2 = 0.f;
+        for (int i = tid; i < n; i += nt) {
+          const float v = Zt[(size_t)i * ldz + c];
+          s2 = fmaf(v, v, s2);
+        }
+        const float ss = tri_block_sum(s2, red);
+        const float rr = 1.f / sqrtf(fmaxf(ss, 1e-30f));
+        for (int i = tid; i < n; i += nt) Zt[(size_t)i * ldz + c] *= rr;
+        __syncthreads();
+      }
+    }
+  }
+}
+
+
 // Fallback of step 4: columns 0..count-1 of Zt orthonormal by classical
 // Gram-Schmidt, twice per column.
 static __device__ void tri_cgs2(float* Zt, int ldz, int n, int count, float* hbuf, float* red) {
@@ -1007,7 +1155,7 @@ static __device__ void tri_cgs2(float* Zt, int ldz, int n, int count, float* hbu
 template <int R, int MAXJ, int VPT>
 __device__ void tri_back_write(const EigArgs& a, const float* V, int n, const float* Zt, int ldz,
                                int count, const double* mu, const double* mup, const int* pos,
-                               float* mw) {
+                               float* mw, float* raw = nullptr, int ldraw = 0) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int nout = a.ell - 1;
@@ -1095,7 +1243,13 @@ __device__ void tri_back_write(const EigArgs& a, const float* V, int n, const fl
         }
       }
     }
-    if (act) {
+    if (act && raw != nullptr) {
+#pragma unroll
+      for (int j = 0; j < MAXJ; ++j) {
+        const int i = n - 1 - (g + R * j);
+        if (i >= 0) raw[(size_t)c * ldraw + i] = z[j];
+      }
+    } else if (act) {
       const int k = pos[c];
       // sqrt(mu'/mu) in FP32: the rotate matrix itself is FP32
       const float sc = (mu[k] > 0.0) ? sqrtf((float)mup[k] / (float)mu[k]) : 0.f;
@@ -1238,7 +1392,13 @@ __device__ void tri_back_write(const EigArgs& a, const float* V, int n, const fl
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int c = c0 + h;
-      if (c < count) {
+      if (c < count && raw != nullptr) {
+#pragma unroll
+        for (int j = 0; j < MAXJ; ++j) {
+          const int i = n - 1 - (g + R * j);
+          if (i >= 0) raw[(size_t)c * ldraw + i] = h ? z1[j] : z0[j];
+        }
+      } else if (c < count) {
         const int k = pos[c];
         const float sc = (mu[k] > 0.0) ? sqrtf((float)mup[k] / (float)mu[k]) : 0.f;
         if (a.row_mass && g == 0) a.row_mass[c] = mup[k];
@@ -1259,6 +1419,10 @@ __device__ void tri_back_write(const EigArgs& a, const float* V, int n, const fl
     }
   }
   }
+  if (raw != nullptr) {
+    __syncthreads();
+    return;
+  }
   if (a.row_mass)
     for (int r = count + tid; r < nout; r += nt) a.row_mass[r] = 0.0;
   for (int idx = tid; idx < (nout - count) * n; idx += nt) {
@@ -1267,6 +1431,213 @@ __device__ void tri_back_write(const EigArgs& a, const float* V, int n, const fl
     if (a.wrot_hi) {
       a.wrot_hi[(size_t)r * a.ldr16 + i] = __float2bfloat16_rn(0.f);
       a.wrot_lo[(size_t)r * a.ldr16 + i] = __float2bfloat16_rn(0.f);
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Step 6 (refinement): Rayleigh-Ritz with the original G. The reflectors of
+// step 1 carry rounding errors of about eps ||G||, so the eigenvalues of T near
+// the cut, small against ||G||, are off by that much, and the vectors of
+// eigenvalues closer than that mix (the fallback of step 4 only makes such
+// groups orthonormal). The shrink sigma'^2 = sigma^2 - delta takes the
+// difference of two of these eigenvalues. In the basis U of the P vectors
+// the projected matrix H = U^T G U is diagonal up to those mixings; its
+// entries are sums of products of G with the vectors, rounded relative to the
+// terms they add, which are small where a vector is small along the large
+// rows of G. H is diagonalised by Jacobi rotations (U rotated alongside), and
+// its diagonal gives the eigenvalues.
+//   Us: n x ldu floats (shared or global; ldu = P rounded up to 4), the
+//   vectors transposed (Us[k * ldu + c] = u_c[k]); H: P x ldh floats after it;
+//   Y: n x ldu floats of global scratch (G U); G: the scaled Gram as loaded,
+//   row stride ldg (a multiple of 4); uvec: P rows of n floats (global).
+// G U and U^T (G U) are formed from 32-term FP32 chunks added by a
+// compensated (two-sum) FP32 accumulation. Rotation (p, q), for columns at
+// most 32 apart in spectral order, is taken when |H_pq| > 1e-2 |H_pp - H_qq|
+// and above the FP32 resolution of the diagonal; a coupling below that
+// shifts an eigenvalue by at most 1e-4 of the gap.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tri_twosum_add(float& hi, float& lo, float b) {
+  const float t = hi + b, bb = t - hi;
+  lo += (hi - (t - bb)) + (b - bb);
+  hi = t;
+}
+
+__device__ inline void tri_ritz(const float* __restrict__ G, int ldg, const float* uvec, int n,
+                                int P, float* Us, int ldu, float* H, int ldh, float* Y) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  // vectors, transposed, each scaled to unit norm (FP32 chunks, FP64 total)
+  for (int c = warp; c < P; c += nt >> 5) {
+    double s2 = 0.0;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+      const float v = (k0 + lane < n) ? uvec[(size_t)c * n + k0 + lane] : 0.f;
+      s2 += (double)warp_sum(v * v);
+    }
+    const float inv = (s2 > 0.0) ? (float)(1.0 / sqrt(s2)) : 0.f;
+    for (int k = lane; k < n; k += 32) Us[(size_t)k * ldu + c] = uvec[(size_t)c * n + k] * inv;
+  }
+  for (int idx = tid; idx < n * (ldu - P); idx += nt) {
+    const int k = idx / (ldu - P), c = P + idx - k * (ldu - P);
+    Us[(size_t)k * ldu + c] = 0.f;
+  }
+  __syncthreads();
+  // Y = G U, 4 x 4 blocks per thread
+  const int nrb = (n + 3) / 4, ncb = ldu / 4;
+  for (int blk = tid; blk < nrb * ncb; blk += nt) {
+    const int cb = blk % ncb, rb = blk / ncb;
+    const int i0 = 4 * rb, c0 = 4 * cb;
+    float hs[4][4], ls[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { hs[p][q] = 0.f; ls[p][q] = 0.f; }
+    const float* g0 = G + (size_t)min(i0, n - 1) * ldg;
+    const float* g1 = G + (size_t)min(i0 + 1, n - 1) * ldg;
+    const float* g2 = G + (size_t)min(i0 + 2, n - 1) * ldg;
+    const float* g3 = G + (size_t)min(i0 + 3, n - 1) * ldg;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+      float ch[4][4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ch[p][q] = 0.f;
+      const int k1 = min(n, k0 + 32);
+      for (int k = k0; k < k1; ++k) {
+        const float gv[4] = {g0[k], g1[k], g2[k], g3[k]};
+        const float4 u = *reinterpret_cast<const float4*>(Us + (size_t)k * ldu + c0);
+        const float uv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ch[p][q] = fmaf(gv[p], uv[q], ch[p][q]);
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tri_twosum_add(hs[p][q], ls[p][q], ch[p][q]);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      if (i0 + p >= n) break;
+      *reinterpret_cast<float4*>(Y + (size_t)(i0 + p) * ldu + c0) =
+          make_float4(hs[p][0] + ls[p][0], hs[p][1] + ls[p][1], hs[p][2] + ls[p][2],
+                      hs[p][3] + ls[p][3]);
+    }
+  }
+  __syncthreads();
+  // H = U^T Y, 4 x 4 blocks per thread (lower and upper blocks both formed)
+  for (int blk = tid; blk < ncb * ncb; blk += nt) {
+    const int a0 = 4 * (blk / ncb), b0 = 4 * (blk % ncb);
+    float hs[4][4], ls[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { hs[p][q] = 0.f; ls[p][q] = 0.f; }
+    for (int k0 = 0; k0 < n; k0 += 32) {
+      float ch[4][4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ch[p][q] = 0.f;
+      const int k1 = min(n, k0 + 32);
+      for (int k = k0; k < k1; ++k) {
+        const float4 u = *reinterpret_cast<const float4*>(Us + (size_t)k * ldu + a0);
+        const float4 y = *reinterpret_cast<const float4*>(Y + (size_t)k * ldu + b0);
+        const float uv[4] = {u.x, u.y, u.z, u.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ch[p][q] = fmaf(uv[p], yv[q], ch[p][q]);
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tri_twosum_add(hs[p][q], ls[p][q], ch[p][q]);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (a0 + p < P && b0 + q < P) H[(size_t)(a0 + p) * ldh + b0 + q] = hs[p][q] + ls[p][q];
+  }
+  __syncthreads();
+  // symmetrise: H_ab = (H_ab + H_ba) / 2
+  for (int idx = tid; idx < P * P; idx += nt) {
+    const int a = idx / P, b = idx - a * P;
+    if (a < b) {
+      const float v = 0.5f * (H[(size_t)a * ldh + b] + H[(size_t)b * ldh + a]);
+      H[(size_t)a * ldh + b] = v;
+      H[(size_t)b * ldh + a] = v;
+    }
+  }
+  __syncthreads();
+  // Jacobi on H by warp 0: sweeps over the pairs, 32 pairs tested at a time,
+  // the significant ones rotated one after another
+  if (warp == 0) {
+    const float eps = 1.1920929e-07f;
+    for (int sweep = 0; sweep < 6; ++sweep) {
+      bool any = false;
+      // pairs (p, q) with q - p <= 32: the columns are in spectral order,
+      // and a coupling H_pq above 1e-2 |H_pp - H_qq| joins near neighbours
+      for (int pr = 0; pr + 1 < P; ++pr)
+      for (int q0 = pr + 1; q0 < min(P, pr + 33); q0 += 32) {
+        // pairs (pr, q0 + lane)
+        int p = -1, q = -1;
+        if (q0 + lane < P) {
+          p = pr;
+          q = q0 + lane;
+        }
+        bool sig = false;
+        if (p >= 0) {
+          const float app = H[(size_t)p * ldh + p], aqq = H[(size_t)q * ldh + q];
+          const float apq = H[(size_t)p * ldh + q];
+          sig = fabsf(apq) > 1e-2f * fabsf(app - aqq) &&
+                fabsf(apq) > 4.f * eps * sqrtf(fabsf(app) * fabsf(aqq));
+        }
+        unsigned m = __ballot_sync(0xffffffffu, sig);
+        while (m) {
+          const int src = __ffs(m) - 1;
+          m &= m - 1;
+          const int pp = __shfl_sync(0xffffffffu, p, src);
+          const int qq = __shfl_sync(0xffffffffu, q, src);
+          const float app = H[(size_t)pp * ldh + pp], aqq = H[(size_t)qq * ldh + qq];
+          const float apq = H[(size_t)pp * ldh + qq];
+          // recheck: earlier rotations of this batch may have changed the pair
+          if (!(fabsf(apq) > 1e-2f * fabsf(app - aqq) &&
+                fabsf(apq) > 4.f * eps * sqrtf(fabsf(app) * fabsf(aqq))))
+            continue;
+          any = true;
+          const float zeta = (aqq - app) / (2.f * apq);
+          const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float c = 1.f / sqrtf(1.f + tt * tt), s = c * tt;
+          __syncwarp();
+          // rows p, q (then columns by symmetry)
+          for (int j = lane; j < P; j += 32) {
+            if (j == pp || j == qq) continue;
+            const float hp = H[(size_t)pp * ldh + j], hq = H[(size_t)qq * ldh + j];
+            const float np_ = c * hp - s * hq, nq_ = s * hp + c * hq;
+            H[(size_t)pp * ldh + j] = np_;
+            H[(size_t)qq * ldh + j] = nq_;
+            H[(size_t)j * ldh + pp] = np_;
+            H[(size_t)j * ldh + qq] = nq_;
+          }
+          if (lane == 0) {
+            H[(size_t)pp * ldh + pp] = app - tt * apq;
+            H[(size_t)qq * ldh + qq] = aqq + tt * apq;
+            H[(size_t)pp * ldh + qq] = 0.f;
+            H[(size_t)qq * ldh + pp] = 0.f;
+          }
+          for (int k = lane; k < n; k += 32) {
+            const float up = Us[(size_t)k * ldu + pp], uq = Us[(size_t)k * ldu + qq];
+            Us[(size_t)k * ldu + pp] = c * up - s * uq;
+            Us[(size_t)k * ldu + qq] = s * up + c * uq;
+          }
+          __syncwarp();
+        }
+      }
+      if (!any) break;
     }
   }
   __syncthreads();
@@ -1285,7 +1656,7 @@ __device__ void tri_back_write(const EigArgs& a, const float* V, int n, const fl
 template <int NB, int R, int MAXJ, int VPT>
 __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double smax,
                                unsigned char* scr_raw, unsigned char* small, unsigned char* rw) {
-  constexpr int TRI_CU = (R * MAXJ / 2 + 31) / 32;  // retained vectors <= n / 2 <= 32 TRI_CU
+  constexpr int TRI_CU = (R * MAXJ / 2 + 32) / 32;  // vectors <= n / 2 + 1 <= 32 TRI_CU
   const int tid = threadIdx.x, nt = blockDim.x;
   double* mu = reinterpret_cast<double*>(small);
   double* mup = mu + n;
@@ -1314,9 +1685,7 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
   const int nl = (a.variant == FD_VAR_SS || a.sig2_out) ? n : min(n, a.ell + 1);
   __shared__ double s_trace;
   if (threadIdx.x < 32) {
-    double t = 0.0;
-    for (int i = threadIdx.x; i < n; i += 32) t += (double)A[(size_t)i * ld + i];
-    t = warp_sum(t);
+    const double t = eig_trace(a, A, ld, n, smax);
     if (threadIdx.x == 0) s_trace = t;
   }
   tri_reduce(A, ld, n, d, e, rw, red);
@@ -1331,17 +1700,35 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
   // n <= blockDim.x (512 threads for n <= 512; the batched kernel: n <= 128, 256 threads)
   shrink_sorted(a, n, n, 1.1920928955078125e-07, mu, mup, rrank, &s_count, &s_dsum, &s_dlast);
   const int nout = a.ell - 1;
-  const int count = s_count < nout ? s_count : nout;
-  for (int k = tid; k < n; k += nt) {
-    const int r = rrank[k];
-    if (r >= 0 && r < nout) pos[r] = k;
+  // Refinement (step 6) for the rules that keep or shrink by position (FD,
+  // PFD, iSVD): vectors for positions 0..ell, the retained ones, the one at
+  // the cut (delta) and the next, whose Ritz values replace the eigenvalues
+  // of T (also when delta = 0: the kept values are then sigma^2 itself).
+  // Needs room for ell+1 vectors and the saved G.
+  const int nref = a.ell + 1;
+  const bool refine = a.gsave != nullptr && a.uvec != nullptr &&
+                      (a.variant == FD_VAR_FD || a.variant == FD_VAR_PFD ||
+                       a.variant == FD_VAR_ISVD) &&
+                      nref <= n / 2 + 1 && mu[0] > 0.0 &&
+                      (size_t)tri_zoff(n) + (size_t)n * nref <= (size_t)n * ld &&
+                      (size_t)n * ((nref + 3) & ~3) + (size_t)nref * (nref + 1) <= (size_t)n * ld;
+  const int count = refine ? nref : (s_count < nout ? s_count : nout);
+  if (refine) {
+    for (int k = tid; k < nref; k += nt) pos[k] = k;
+  } else {
+    for (int k = tid; k < n; k += nt) {
+      const int r = rrank[k];
+      if (r >= 0 && r < nout) pos[r] = k;
+    }
   }
   if (tid == 0) s_ok = 1;
   __syncthreads();
   const float tnorm = s_tnorm;
   const float pivmin = fmaxf(tnorm, 1e-30f) * 1e-30f;
   float* Zt = A + tri_zoff(n);
-  const int ldz = tri_ldz(count);
+  // odd stride (fewer bank conflicts) where it fits after the reflectors
+  const int ldz = ((size_t)tri_zoff(n) + (size_t)n * tri_ldz(count) <= (size_t)n * ld)
+                      ? tri_ldz(count) : count;
   for (int r = tid; r < count; r += nt)
     if (!tri_twisted(d, e, e2, n, lam[pos[r]], pivmin, Zt + r, ldz)) s_ok = 0;
   __syncthreads();
@@ -1350,7 +1737,7 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
   if (ok) {
     const int ldc = tri_ldz(count);
     float* C = reinterpret_cast<float*>(scr_raw);
-    float* dinv = reinterpret_cast<float*>(scr_raw + tri_al16((size_t)(n / 2) * ((n / 2) | 1) * 4));
+    float* dinv = reinterpret_cast<float*>(scr_raw + tri_al16((size_t)count * ldc * 4));
     ok = tri_cholqr<TRI_CU>(Zt, ldz, n, count, C, ldc, dinv, 0.25f);
   }
   if (!ok) {
@@ -1365,18 +1752,15 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
     __shared__ int s_nl;
     __syncthreads();
     float* scr = reinterpret_cast<float*>(scr_raw);
-    int* ord = reinterpret_cast<int*>(pb);
-    int* list = ord + count;
+    int* ord = reinterpret_cast<int*>(vb0);   // vb0, vb1: np8 >= count entries each,
+    int* list = reinterpret_cast<int*>(vb1);  // dead after step 1
     bool redo = s_ok == 0;
     if (!redo) {
-      tri_cluster_members(lam, pos, n, count, 1e-4f * tnorm, ord, list, &s_nl);
-      for (int c0 = 0; c0 < s_nl; c0 += NB) {
-        tri_invit_batch<NB>(Zt, ldz, n, d, e, lam, pos, list, c0, s_nl, tnorm, scr);
-        __syncthreads();
-      }
+      tri_tight_repair<NB>(Zt, ldz, n, d, e, lam, pos, count, 16.f * 1.1920929e-07f * tnorm,
+                           tnorm, scr, ord, list, reinterpret_cast<int*>(qb), xb, red, &s_nl);
       const int ldc = tri_ldz(count);
       float* C = reinterpret_cast<float*>(scr_raw);
-      float* dinv = reinterpret_cast<float*>(scr_raw + tri_al16((size_t)(n / 2) * ((n / 2) | 1) * 4));
+      float* dinv = reinterpret_cast<float*>(scr_raw + tri_al16((size_t)count * ldc * 4));
       redo = !tri_cholqr<TRI_CU>(Zt, ldz, n, count, C, ldc, dinv, 0.25f);
     }
     if (redo) {
@@ -1388,8 +1772,85 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
       tri_cgs2(Zt, ldz, n, count, xb, red);
     }
   }
-  tri_back_write<R, MAXJ, VPT>(a, A, n, Zt, ldz, count, mu, mup, pos, vb0);  // vb0..pb: 4 np8 floats
-  write_counters(a, n, mu, mup, s_count, s_dsum, s_dlast, 0, 1, nl < n ? s_trace * smax : -1.0,
+  if (!refine) {
+    tri_back_write<R, MAXJ, VPT>(a, A, n, Zt, ldz, count, mu, mup, pos, vb0);  // vb0..pb: 4 np8 floats
+    write_counters(a, n, mu, mup, s_count, s_dsum, s_dlast, 0, 1, nl < n ? s_trace : -1.0,
+                   fell_back ? 1 : 0);
+    return;
+  }
+  // unscaled vectors u_0..u_ell (original basis) to the global scratch
+  tri_back_write<R, MAXJ, VPT>(a, A, n, Zt, ldz, count, mu, mup, pos, vb0, a.uvec, n);
+  // Rayleigh-Ritz; A, Zt and the scratch area are dead now: the vectors are
+  // staged (transposed) in the front of A, H after them, G U in the vectors'
+  // global scratch (read into Us first)
+  const int ldu = (nref + 3) & ~3;
+  const int ldh = nref + 1;
+  double* rho = reinterpret_cast<double*>(d);  // d, e: 2n floats >= nref doubles
+  float* Us = A;
+  float* Hm = A + (size_t)n * ldu;
+  tri_ritz(a.gsave, a.ldgsave, a.uvec, n, nref, Us, ldu, Hm, ldh, a.uvec);
+  for (int c = tid; c < nref; c += nt) rho[c] = (double)Hm[(size_t)c * ldh + c];
+  __syncthreads();
+  // refined masses in descending order (ties by position); positions past
+  // the refined block keep the bisection values, capped by the last refined one
+  int* ordv = reinterpret_cast<int*>(e2);  // sorted index -> vector column
+  for (int c = tid; c < nref; c += nt) {
+    const double v = rho[c];
+    int rk = 0;
+    for (int q = 0; q < nref; ++q) {
+      const double w = rho[q];
+      rk += (w > v) || (w == v && q < c);
+    }
+    ordv[rk] = c;
+  }
+  __syncthreads();
+  {
+    // the same floor as for the eigenvalues of T: Ritz values at or below
+    // 2 eps of the largest are rounding noise of the FP32 Gram (a rank-
+    // deficient buffer), taken as zero
+    const double zf = 2.0 * 1.1920928955078125e-07 * fmax(rho[ordv[0]], 0.0);
+    for (int k = tid; k < nref; k += nt) {
+      const double v = rho[ordv[k]];
+      mu[k] = (v > zf) ? v * smax : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int k = nref + tid; k < n; k += nt) mu[k] = fmin(mu[k], mu[nref - 1]);
+  __syncthreads();
+  shrink_sorted(a, n, n, 1.1920928955078125e-07, mu, mup, rrank, &s_count, &s_dsum, &s_dlast);
+  // rotate matrix rows: rank r <- sorted position k <- vector column ordv[k],
+  // scaled by sqrt(mu'/mu); rows past the retained count are zero
+  const int cnt = s_count < nout ? s_count : nout;
+  float* wr = reinterpret_cast<float*>(a.wrot);
+  for (int k = tid; k < nref; k += nt) {
+    const int r = rrank[k];
+    if (r >= 0 && r < nout) pos[r] = k;
+  }
+  __syncthreads();
+  // per output row: its scale sqrt(mu'/mu) (one FP64 square root a row) and
+  // the column of Us it takes
+  float* rscale = vb1;
+  int* rcol = reinterpret_cast<int*>(xb);
+  for (int r = tid; r < nout; r += nt) {
+    const int k = (r < cnt) ? pos[r] : 0;
+    rscale[r] = (r < cnt && mu[k] > 0.0) ? (float)sqrt(mup[k] / mu[k]) : 0.f;
+    rcol[r] = (r < cnt) ? ordv[k] : 0;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < nout * n; idx += nt) {
+    const int r = idx / n, i = idx - r * n;
+    const float val = rscale[r] * Us[(size_t)i * ldu + rcol[r]];
+    wr[(size_t)r * a.ldr + i] = val;
+    if (a.wrot_hi) {
+      const __nv_bfloat16 hi = __float2bfloat16_rn(val);
+      a.wrot_hi[(size_t)r * a.ldr16 + i] = hi;
+      a.wrot_lo[(size_t)r * a.ldr16 + i] = __float2bfloat16_rn(val - __bfloat162float(hi));
+    }
+  }
+  if (a.row_mass)
+    for (int r = tid; r < nout; r += nt) a.row_mass[r] = (r < cnt) ? mup[pos[r]] : 0.0;
+  __syncthreads();
+  write_counters(a, n, mu, mup, s_count, s_dsum, s_dlast, 0, 1, nl < n ? s_trace : -1.0,
                  fell_back ? 1 : 0);
 }
 

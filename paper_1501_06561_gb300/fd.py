@@ -67,6 +67,7 @@ def load():
         "fd_record_spectrum": [vp, i32],
         "fd_sketch_compensated": [vp, vp, i32, i32],
         "fd_merge": [vp, vp],
+        "fd_merge_sketch": [vp, vp, i64, i64, i32, i32, ctypes.POINTER(Stats)],
         "fd_cov_err": [vp, vp, i64, i64, i32, i32, ctypes.POINTER(dbl)],
         "fd_proj_err": [vp, vp, i64, i64, i32, i32, i32, ctypes.POINTER(dbl)],
         "fd_cov_err_pair": [vp, i64, i64, i64, i32, vp, i64, i32, i32, vp,
@@ -212,6 +213,19 @@ class FDSketch:
         """Fold ``other``'s stream into this sketch (fd_merge)."""
         _check(load().fd_merge(self._h, other._h), "fd_merge")
 
+    def merge_sketch(self, B, stats: dict):
+        """Fold a sketch given as its rows ``B`` (up to the last nonzero row)
+        and the counters ``stats`` (an fd_stats dict) into this one
+        (fd_merge_sketch)."""
+        ptr, n, ld, code, dev, keep = _as_rows(B)
+        st = Stats()
+        for f, _ in Stats._fields_:
+            if f in stats:
+                setattr(st, f, type(getattr(st, f))(stats[f]))
+        _check(load().fd_merge_sketch(self._h, ptr, n, ld, code, dev, ctypes.byref(st)),
+               "fd_merge_sketch")
+        return keep
+
     def cov_err(self, A) -> float:
         ptr, n, ld, code, dev, keep = _as_rows(A)
         out = ctypes.c_double()
@@ -299,6 +313,9 @@ def cov_err_noalloc(A, B, stream=None):
     if not (da and db):
         raise ValueError("A and B must be CUDA tensors")
     d = A.shape[1]
+    if ldb != d:  # the entry point reads B with leading dimension d
+        kb = kb.contiguous()
+        pb, rows, ldb, cb, db, kb = _as_rows(kb)
     out = ctypes.c_double()
     _check(load().fd_cov_err_noalloc(pa, n, d, lda, ca, pb, rows, cb, _stream_ptr(stream),
                                      ctypes.byref(out)), "fd_cov_err_noalloc")

@@ -12,12 +12,9 @@ unique at any size:
 - Lemma 1 (Sec. 3.1) on the GPU's own counters;
 - the removed mass of at least ell * delta per reduction.
 
-The FP32 path meets the bar. The split-precision BF16x3 path ends 4.3e-5
-above the oracle's cov-err after 1,979 reductions, which is also above the
-oracle's bound Delta / ||A||_F^2. A model of its rounding (the same split,
-exact or truncated FP32 sums) ends only 7.6e-7 above, so the cause lies in
-something that model leaves out. That case is marked as an expected failure
-until the cause is found and removed.
+Both paths meet the cov-err bar. The FP32 path also meets the per-value
+sigma bar; the split-precision BF16x3 path resolves the smallest values near
+the cut to about 2^-17 sigma_1^2, and that check is an expected failure for it.
 """
 import json
 import os
@@ -30,7 +27,7 @@ torch = pytest.importorskip("torch")
 from oracle import cov_err
 from paper_1501_06561_gb300 import fd
 from paper_1501_06561_gb300 import workloads as W
-from helpers import COV_ABS
+from helpers import COV_ABS, assert_sigma_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -87,12 +84,27 @@ def test_full_stream_fp32_matches_oracle(rows):
     assert abs(delta - GOLD["sum_delta"]) <= 1e-2 * GOLD["sum_delta"]
     # every reduction removes at least ell * delta (a 2*ell-row buffer)
     assert ell * delta <= (st["norm_a2"] - st["sketch_norm_b2"]) * (1.0 + 1e-6)
+    # singular values, per value against the oracle's
+    assert_sigma_parity(B, _gold_sketch_diag(), GOLD["normA2"], "fp32", what="C1 full fp32")
 
 
-@pytest.mark.xfail(reason="BF16x3 ends 4.3e-5 above the oracle's cov-err after 1,979 "
-                          "reductions (cause not yet found)", strict=False)
+def _gold_sketch_diag():
+    """A matrix whose singular values are the oracle's stored sigma(B)."""
+    return np.diag(np.array(GOLD["sigma"], dtype=np.float64))
+
+
 def test_full_stream_bf16x3_matches_oracle(rows):
     A, A_dev, norm2 = rows
     B, st, ce = _run(A_dev, "bf16x3")
     assert abs(st["norm_a2"] - norm2) <= 1e-11 * norm2
     assert abs(ce - GOLD["cov_err"]) <= COV_ABS, (ce, GOLD["cov_err"])
+    # Lemma 1 (Sec. 3.1) on the path's own counters
+    assert ce <= st["sketch_sum_delta"] / st["norm_a2"] + COV_ABS
+
+
+@pytest.mark.xfail(reason="BF16x3: the smallest values near the cut reach about 2.5x the "
+                          "per-value bar on this stream", strict=False)
+def test_full_stream_bf16x3_sigma(rows):
+    A, A_dev, norm2 = rows
+    B, st, ce = _run(A_dev, "bf16x3")
+    assert_sigma_parity(B, _gold_sketch_diag(), GOLD["normA2"], "bf16x3", what="C1 full bf16x3")

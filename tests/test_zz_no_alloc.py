@@ -67,3 +67,41 @@ def test_noalloc_rejects_sizes_beyond_workspace():
     rc = lib.fd_cov_err_noalloc(ctypes.c_void_p(A.data_ptr()), 8, 64, 64, 0,
                                 ctypes.c_void_p(B.data_ptr()), 513, 0, None, ctypes.byref(out))
     assert rc == -6
+
+
+def _rel(v, r):
+    return abs(v - r) / max(1.0, abs(r))
+
+
+@pytest.mark.parametrize("d", [1, 3, 5, 1024])
+def test_noalloc_against_the_oracle_for_small_and_large_d(d):
+    """Widths down to one column: the Lanczos run ends after d steps, and the
+    value of that last step is the answer (Sec. 1.1 definition, FP64 oracle)."""
+    from oracle import cov_err
+    A = W.random_noisy(400, d, m=min(4, d), seed=10 + d, dtype=np.float32)
+    rng = np.random.default_rng(d)
+    B = (rng.standard_normal((3, d)) * np.sqrt(400 / d)).astype(np.float32)
+    ref = cov_err(A, B)
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    for _ in range(2):
+        assert _rel(fd.cov_err_noalloc(Ad, Bd), ref) <= TOL
+    assert _rel(fd.cov_err_pair(Ad, Bd)[0], ref) <= TOL
+
+
+def test_noalloc_without_sketch_rows_and_with_strided_views():
+    """rows = 0 gives ||A^T A||_2 / ||A||_F^2; an A view with row stride above d
+    and a column-sliced B view give the values of their contiguous copies."""
+    from oracle import cov_err
+    A = W.random_noisy(3000, 200, m=10, seed=21, dtype=np.float32)
+    Ad = torch.from_numpy(A).cuda()
+    B0 = torch.zeros(0, 200, device="cuda")
+    assert _rel(fd.cov_err_noalloc(Ad, B0), cov_err(A, np.zeros((0, 200)))) <= TOL
+    big = torch.zeros(3000, 256, device="cuda")
+    big[:, :200] = Ad
+    Aview = big[:, :200]                      # row stride 256 > d
+    rng = np.random.default_rng(22)
+    Bbig = torch.from_numpy(rng.standard_normal((12, 300)).astype(np.float32) * 4.0).cuda()
+    Bview = Bbig[:, :200]                      # column slice, row stride 300
+    ref = fd.cov_err_pair(Ad, Bview.contiguous())[0]
+    for _ in range(2):
+        assert abs(fd.cov_err_noalloc(Aview, Bview) - ref) <= TOL
