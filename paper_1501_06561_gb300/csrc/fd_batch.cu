@@ -164,8 +164,8 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
   for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
   if ((tid & 31) == 0) atomicMax(reinterpret_cast<int*>(&s_max), __float_as_int(dm));
   __syncthreads();
-  const float smax = s_max;
-  const float inv = smax > 0.f ? 1.f / smax : 1.f;
+  const float smax = eig_pow2_scale(s_max);
+  const float inv = 1.f / smax;  // exact: smax is a power of two
   for (int idx = tid; idx < nz * ld; idx += BT) A[idx] *= inv;
   __syncthreads();
   if (tri) {

@@ -81,6 +81,65 @@ __device__ void eig_load(const EigArgs& a, T* Wm, int ld, int n, int np) {
   }
 }
 
+// eig_load for a row-major G in shared memory (stride ld >= n): the partial
+// slices summed row by row with coalesced loads, several in flight per lane,
+// then symmetrised in place, G_ij = (Z_ij + Z_ji) / 2 (the values eig_load
+// gives), and the exact diagonal put in when eig_prepare_diag supplied one.
+// Columns n..ld-1 are zeroed. Ends with a block barrier.
+template <typename T>
+__device__ void eig_load_sym(const EigArgs& a, T* Wm, int ld, int n) {
+  const T* parts = reinterpret_cast<const T*>(a.parts);
+  const int nv = (a.nvalid > 0 && a.nvalid < n) ? a.nvalid : n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  constexpr int U = 8;
+  for (int i = warp; i < n; i += nw) {
+    T* row = Wm + (size_t)i * ld;
+    for (int j0 = 0; j0 < ld; j0 += 32 * U) {
+      T v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = T(0);
+      if (i < nv) {
+        for (int p = 0; p < a.nparts; ++p) {
+          const T* src = parts + (int64_t)p * a.part_stride + (int64_t)i * a.ldp;
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int j = j0 + lane + 32 * u;
+            if (j < nv) v[u] += src[j];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = j0 + lane + 32 * u;
+        if (j < ld) row[j] = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = warp; i < n; i += nw) {
+    for (int j = i + 1 + lane; j < n; j += 32) {
+      const T v = T(0.5) * (Wm[(size_t)i * ld + j] + Wm[(size_t)j * ld + i]);
+      Wm[(size_t)i * ld + j] = v;
+      Wm[(size_t)j * ld + i] = v;
+    }
+  }
+  if (a.diag64 != nullptr)
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) Wm[(size_t)i * ld + i] = (T)a.diag64[i];
+  __syncthreads();
+}
+
+// Scale of the Gram before an FP32 eigensolve: the power of two at or above
+// its largest diagonal entry smax (1 for an empty Gram). Multiplying by a
+// power of two is exact; a factor fl(1/smax) would move every eigenvalue by
+// the same relative amount (up to 2^-24), and since FD subtracts delta at
+// every reduction, that shift would add up along a stream.
+__device__ __forceinline__ float eig_pow2_scale(float smax) {
+  if (!(smax > 0.f)) return 1.f;
+  int e;
+  (void)frexpf(smax, &e);  // smax = f 2^e, f in [0.5, 1)
+  return ldexpf(1.f, e);
+}
+
 // FP64 trace of the loaded G: the exact diagonal when it is known, else the
 // diagonal of Wm (scaled back by wscale). One warp (threads 0..31); the
 // result is valid in lane 0.

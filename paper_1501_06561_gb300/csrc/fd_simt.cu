@@ -347,8 +347,8 @@ __global__ void __launch_bounds__(NT) eig_fast_kernel(EigArgs a) {
   for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
   if ((tid & 31) == 0) atomicMax(reinterpret_cast<int*>(&s_max), __float_as_int(dm));
   __syncthreads();
-  const float smax = s_max;
-  const float inv = (smax > 0.f) ? 1.f / smax : 1.f;
+  const float smax = eig_pow2_scale(s_max);
+  const float inv = 1.f / smax;  // exact: smax is a power of two
   for (int idx = tid; idx < np * ld; idx += blockDim.x) Wm[idx] *= inv;
   __syncthreads();
   int capped = 0;
@@ -376,23 +376,30 @@ __global__ void __launch_bounds__(512, 1) eig_tri_kernel(EigArgs a) {
   // (tri_config checks that it is large enough), else after `small`
   unsigned char* rw = GLOBAL ? smem_raw + tri_small_bytes(n) : scr;
   __shared__ float s_max;
-  eig_prepare_diag(a, n);
-  eig_load<float>(a, A, ld, n, n);
   if (tid == 0) s_max = 0.f;
-  __syncthreads();
+  eig_prepare_diag(a, n);
+  eig_load_sym<float>(a, A, ld, n);
   float dm = 0.f;
   for (int i = tid; i < n; i += blockDim.x) dm = fmaxf(dm, fabsf(A[(size_t)i * ld + i]));
   for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
   if ((tid & 31) == 0) atomicMax(reinterpret_cast<int*>(&s_max), __float_as_int(dm));
   __syncthreads();
-  const float smax = s_max;
-  const float inv = (smax > 0.f) ? 1.f / smax : 1.f;
-  for (int idx = tid; idx < n * ld; idx += blockDim.x) A[idx] *= inv;
-  __syncthreads();
-  if (a.gsave != nullptr) {  // the scaled G, kept for the Rayleigh quotients
-    for (int idx = tid; idx < n * a.ldgsave; idx += blockDim.x) {
-      const int i = idx / a.ldgsave, j = idx - i * a.ldgsave;
-      a.gsave[idx] = (j < n) ? A[(size_t)i * ld + j] : 0.f;
+  const float smax = eig_pow2_scale(s_max);
+  const float inv = 1.f / smax;  // exact: smax is a power of two
+  {
+    // scale; the scaled G is also kept (gsave) for the Rayleigh quotients
+    const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int wcols = (a.gsave != nullptr && a.ldgsave > ld) ? a.ldgsave : ld;
+    for (int i = warp; i < n; i += nw) {
+      for (int j = lane; j < wcols; j += 32) {
+        float v = 0.f;
+        if (j < ld) {
+          v = A[(size_t)i * ld + j] * inv;
+          A[(size_t)i * ld + j] = v;
+        }
+        if (a.gsave != nullptr && j < a.ldgsave)
+          a.gsave[(size_t)i * a.ldgsave + j] = (j < n) ? v : 0.f;
+      }
     }
     __syncthreads();
   }
@@ -413,8 +420,8 @@ cudaError_t launch_tri(const EigArgs& a, size_t smem, cudaStream_t st) {
 }
 
 // Whether a reduction of n rows takes the tridiagonal eigensolve: buffers of
-// at least 2*ell rows (the caller passes use_tri only for full buffers;
-// flushes of a partial buffer keep Jacobi). 1: n <= 128 in
+// at least 2*ell rows (a flush of a partial buffer is solved at the full
+// buffer size, its missing rows zero). 1: n <= 128 in
 // shared memory; 2, 3: up to 206 rows in shared memory (LU batches of 16 or 8
 // vectors for the fallback path); 4: up to 512 rows with A and the scratch
 // area in a global workspace of tri_global_bytes(n, 16) bytes.

@@ -197,6 +197,20 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, int* e
 
 // Epilogue: drain accumulator b (columns b*128 .. b*128 + 32*nch - 1 of this
 // warp's 32 lanes) into acc with round-to-nearest adds.
+// A tcgen05.mma result rounds toward zero: each step's value is short of the
+// exact sum of its products by part of an ulp, always on the side of zero,
+// and over the K steps of a product, and over the reductions of a stream,
+// those shortfalls add up (uncorrected, the sketch lost about 1e-6 of each
+// row's mass at every rotate at 2*ell = 200). The correction is
+// proportional to each step's value, so the corrections of all steps sum to
+// one factor times the accumulated sum, applied once at the end: kTcRound
+// per rounding in a step. Half an ulp (a uniformly distributed discarded
+// fraction) would be 2^-24 / (2 ln 2) of a value with log-uniform mantissa;
+// the shortfall measured through the rotate's row masses on the Random
+// Noisy stream (d = 2,000, ell = 100) is smaller, about 2^-25 of the value
+// (many step sums need no rounding at all), and that is the factor used.
+constexpr float kTcRound = 2.9802322e-08f;  // 2^-25
+
 template <int NCH>
 __device__ __forceinline__ void drain_add(uint32_t taddr, int q, int b, int nch, float* acc) {
 #pragma unroll
@@ -331,7 +345,7 @@ __global__ void __launch_bounds__(TC_NT, 1)
       if (lane == 0) mbar_arrive(&accfree[b]);
     }
 #pragma unroll
-    for (int i = 0; i < 128; ++i) part[r * GRAM_PLD + i] = acc[i];
+    for (int i = 0; i < 128; ++i) part[r * GRAM_PLD + i] = fmaf(acc[i], 2.f * kTcRound, acc[i]);  // two roundings a step
   }
   __syncwarp();  // the producer and MMA lanes rejoin their warps
   tc_fence_before();
@@ -483,14 +497,17 @@ __global__ void __launch_bounds__(TC_NT, 1)
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
         const int jl = c * 32 + i, j = n0 + jl;
-        const float x = acc[c * 32 + i];
+        const float x0 = acc[c * 32 + i];
         float sq = 0.0f;
         if (live && jl < NC && j < nout) {
           if (out_rows) {
-            out_rows[(int64_t)j * ldo + m] = x;
+            out_rows[(int64_t)j * ldo + m] = fmaf(x0, kTcRound, x0);  // one rounding a step (hi.hi)
           } else {
-            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-            const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+            // the correction goes into the low part, where it is far above
+            // the rounding unit (x0 - hi is exact)
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x0);
+            const __nv_bfloat16 lo =
+                __float2bfloat16_rn(fmaf(x0, kTcRound, x0 - __bfloat162float(hi)));
             cm_hi[m * ld_cm + j] = hi;
             cm_lo[m * ld_cm + j] = lo;
             rm_hi[(int64_t)j * ld_rm + m] = hi;

@@ -444,6 +444,14 @@ static __device__ void tri_bisect(const float* d, const float* e, float* e2, int
   const float atol = 2.f * eps * tnorm;
   const float lo0 = glo - 0.01f * (ghi - glo) - atol;
   const float hi0 = ghi + 0.01f * (ghi - glo) + atol;
+  // Intervals are refined to a width of 2 eps |lambda| (relative), down to
+  // pivmin-level absolute widths: the eigenvalues near the cut are small
+  // against ||T||, and a twisted vector taken at a shift that is off by
+  // eps ||T|| mixes in its neighbours at that scale, which the Rayleigh-Ritz
+  // step cannot undo for neighbours outside its subspace. The FP32 Sturm
+  // counts of T resolve those eigenvalues to relative accuracy. Widths of
+  // eps^2 ||T|| end the refinement (values that small count as zero later).
+  const float rtol_abs = fmaxf(eps * eps * tnorm, 1e3f * pivmin);
   const float h = (hi0 - lo0) / (float)(nt + 1);
   // grid pass: counts at lo0 + (p + 1) h, p = 0..nt-1 (non-decreasing in p)
   cnt[tid] = tri_sturm(d, e2, n, lo0 + (float)(tid + 1) * h, pivmin);
@@ -468,7 +476,7 @@ static __device__ void tri_bisect(const float* d, const float* e, float* e2, int
       if (b < nt) hi = lo0 + (float)(b + 1) * h;
     }
     for (int it = 0; it < 64; ++it) {
-      const bool done = !act || (hi - lo <= atol + 2.f * eps * fmaxf(fabsf(lo), fabsf(hi)));
+      const bool done = !act || (hi - lo <= rtol_abs + 2.f * eps * fmaxf(fabsf(lo), fabsf(hi)));
       if (__all_sync(0xffffffffu, done)) break;
       const float x = lo + (hi - lo) * (float)(sub + 1) / (float)(G + 1);
       const int c = act ? tri_sturm(d, e2, n, x, pivmin) : 0;
@@ -1464,7 +1472,7 @@ __device__ __forceinline__ void tri_twosum_add(float& hi, float& lo, float b) {
   hi = t;
 }
 
-__device__ inline void tri_ritz(const float* __restrict__ G, int ldg, const float* uvec, int n,
+__device__ inline void tri_ritz(const float* G, int ldg, const float* uvec, int n,
                                 int P, float* Us, int ldu, float* H, int ldh, float* Y) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -1493,10 +1501,9 @@ __device__ inline void tri_ritz(const float* __restrict__ G, int ldg, const floa
     for (int p = 0; p < 4; ++p)
 #pragma unroll
       for (int q = 0; q < 4; ++q) { hs[p][q] = 0.f; ls[p][q] = 0.f; }
-    const float* g0 = G + (size_t)min(i0, n - 1) * ldg;
-    const float* g1 = G + (size_t)min(i0 + 1, n - 1) * ldg;
-    const float* g2 = G + (size_t)min(i0 + 2, n - 1) * ldg;
-    const float* g3 = G + (size_t)min(i0 + 3, n - 1) * ldg;
+    // G is symmetric: rows i0..i0+3 at column k are row k at columns
+    // i0..i0+3, one four-wide load (columns n..ldg-1 hold zeros)
+    const float* gk = G + i0;
     for (int k0 = 0; k0 < n; k0 += 32) {
       float ch[4][4];
 #pragma unroll
@@ -1505,7 +1512,8 @@ __device__ inline void tri_ritz(const float* __restrict__ G, int ldg, const floa
         for (int q = 0; q < 4; ++q) ch[p][q] = 0.f;
       const int k1 = min(n, k0 + 32);
       for (int k = k0; k < k1; ++k) {
-        const float gv[4] = {g0[k], g1[k], g2[k], g3[k]};
+        const float4 g4 = *reinterpret_cast<const float4*>(gk + (size_t)k * ldg);
+        const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
         const float4 u = *reinterpret_cast<const float4*>(Us + (size_t)k * ldu + c0);
         const float uv[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
@@ -1527,9 +1535,17 @@ __device__ inline void tri_ritz(const float* __restrict__ G, int ldg, const floa
     }
   }
   __syncthreads();
-  // H = U^T Y, 4 x 4 blocks per thread (lower and upper blocks both formed)
-  for (int blk = tid; blk < ncb * ncb; blk += nt) {
-    const int a0 = 4 * (blk / ncb), b0 = 4 * (blk % ncb);
+  // H = U^T Y, 4 x 4 blocks per thread: the blocks on and above the
+  // diagonal, each mirrored below it
+  const int nhb = ncb * (ncb + 1) / 2;
+  for (int blk = tid; blk < nhb; blk += nt) {
+    // blk -> (ab, bb), ab <= bb; block row ab starts at ab * ncb - ab (ab - 1) / 2
+    int ab = (int)((2.f * ncb + 1.f - sqrtf((2.f * ncb + 1.f) * (2.f * ncb + 1.f) - 8.f * blk)) * 0.5f);
+    ab = max(0, min(ab, ncb - 1));
+    while (ab > 0 && ab * ncb - ab * (ab - 1) / 2 > blk) --ab;
+    while (ab + 1 < ncb && (ab + 1) * ncb - (ab + 1) * ab / 2 <= blk) ++ab;
+    const int bb = ab + (blk - (ab * ncb - ab * (ab - 1) / 2));
+    const int a0 = 4 * ab, b0 = 4 * bb;
     float hs[4][4], ls[4][4];
 #pragma unroll
     for (int p = 0; p < 4; ++p)
@@ -1560,7 +1576,11 @@ __device__ inline void tri_ritz(const float* __restrict__ G, int ldg, const floa
     for (int p = 0; p < 4; ++p)
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (a0 + p < P && b0 + q < P) H[(size_t)(a0 + p) * ldh + b0 + q] = hs[p][q] + ls[p][q];
+        if (a0 + p < P && b0 + q < P) {
+          const float v = hs[p][q] + ls[p][q];
+          H[(size_t)(a0 + p) * ldh + b0 + q] = v;
+          if (a0 != b0) H[(size_t)(b0 + q) * ldh + a0 + p] = v;
+        }
   }
   __syncthreads();
   // symmetrise: H_ab = (H_ab + H_ba) / 2

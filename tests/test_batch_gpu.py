@@ -85,7 +85,6 @@ def test_batch_split_appends_bit_identical():
             np.testing.assert_array_equal(b1.sketch(i), b2.sketch(i))
 
 
-@_XF_BATCH
 def test_batch_equals_single_handles():
     """Each sketch in the mix gives the result it gives alone (single handle,
     FP32 path) within the parity tolerance."""

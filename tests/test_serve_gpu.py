@@ -25,7 +25,6 @@ def _cuda():
     fd.load()
 
 
-@pytest.mark.xfail(reason="the batched kernel's eigensolve has no Rayleigh-Ritz refinement: values just above the cut miss the per-value 1e-4 bar (up to 2.6x)", strict=False)
 def test_serving_mix_equals_solo():
     count, d, ell = 40, 96, 8
     rng = np.random.default_rng(3)
