@@ -31,6 +31,10 @@ constexpr int GB = (528 + BT - 1) / BT;  // Gram 4x4 blocks per thread (<= 528 b
 constexpr int BMAX_L = 128;       // largest buffer (2*ell) a batched sketch may have
 constexpr int KCH = 32;           // Gram K chunk
 constexpr int RCH = 64;           // rotate column chunk
+// Global workspace of one CTA for the Rayleigh-Ritz refinement of a full
+// buffer: the scaled Gram (BMAX_L rows, stride BMAX_L) and the vectors /
+// G U products ((BMAX_L / 2 + 4) x BMAX_L floats).
+constexpr size_t BATCH_WS_FLOATS = (size_t)BMAX_L * BMAX_L + (size_t)(BMAX_L / 2 + 4) * BMAX_L;
 
 struct BatchSketch {
   long long d, ldb;
@@ -72,7 +76,8 @@ constexpr size_t BATCH_SMEM = REG_A + REST;
 // `out` (stride ldo; may be S.buf itself), counters from cin to cout.
 __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long long ldo,
                              const DevCounters* cin, DevCounters* cout, int variant,
-                             double alpha, int max_sweeps, double tol, unsigned char* smem) {
+                             double alpha, int max_sweeps, double tol, unsigned char* smem,
+                             float* ws = nullptr) {
   const int tid = threadIdx.x;
   float* A = reinterpret_cast<float*>(smem);
   float* Bst = reinterpret_cast<float*>(smem + REG_A);
@@ -181,6 +186,19 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
     a.ldr = np;
     a.max_sweeps = max_sweeps;
     a.row_mass = s_mass;
+    if (ws != nullptr) {
+      // Rayleigh-Ritz refinement with the scaled G (as for a single sketch)
+      const int ldg = (nrows + 3) & ~3;
+      float* gsave = ws;
+      for (int idx = tid; idx < nrows * ldg; idx += BT) {
+        const int i = idx / ldg, j = idx - i * ldg;
+        gsave[idx] = (j < nrows) ? A[i * ld + j] : 0.f;
+      }
+      __syncthreads();
+      a.gsave = gsave;
+      a.ldgsave = ldg;
+      a.uvec = ws + (size_t)BMAX_L * BMAX_L;
+    }
     // step 1 of the solve works in the scratch area (272 n >= tri_rw_bytes(n, 8) bytes)
     tri_eig_shrink<TRI_NB, 4, 32, 1>(a, A, ld, nrows, smax > 0.f ? (double)smax : 1.0, smem + REG_A,
                                      smem + REG_A + tri_scratch_bytes(nrows, TRI_NB), smem + REG_A);
@@ -276,7 +294,7 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
 __global__ void __launch_bounds__(BT, 2)
     batch_kernel(BatchSketch* __restrict__ sk, const BatchItem* __restrict__ items, int nitems,
                  int* __restrict__ next, int variant, double alpha, int max_sweeps,
-                 double tol) {
+                 double tol, float* ws_all) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   __shared__ double s_rn[BMAX_L];
@@ -316,7 +334,8 @@ __global__ void __launch_bounds__(BT, 2)
       i += c;
       if (m == S.L) {
         __syncthreads();
-        batch_reduce(S, S.L, S.buf, S.ldb, S.ctr, S.ctr, variant, alpha, max_sweeps, tol, smem);
+        batch_reduce(S, S.L, S.buf, S.ldb, S.ctr, S.ctr, variant, alpha, max_sweeps, tol, smem,
+                     ws_all ? ws_all + (size_t)blockIdx.x * BATCH_WS_FLOATS : nullptr);
         m = S.ell - 1;
       }
       __syncthreads();
@@ -390,6 +409,7 @@ struct fd_batch_state {
   int max_sweeps = 30;
   long long* doffs = nullptr;     // device copy of the sketch_all offsets
   DevCounters* fctr_all = nullptr;
+  float* ws = nullptr;            // 2 * nsm CTA workspaces (BATCH_WS_FLOATS each)
 };
 
 static int batch_fail(cudaError_t e, const char* w) {
@@ -465,6 +485,8 @@ extern "C" int fd_batch_create(int32_t count, const int64_t* d, const int32_t* e
   int dev = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaMalloc(&b->ws, (size_t)2 * b->nsm * BATCH_WS_FLOATS * sizeof(float));
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
   if (e != cudaSuccess) {
     fd_batch_destroy(b);
@@ -512,7 +534,7 @@ extern "C" int fd_batch_append(fd_batch_state* b, const fd_work_t* items, int32_
   const double eps = 1.1920928955078125e-07;
   batch_kernel<<<grid, BT, BATCH_SMEM, b->st>>>(b->dsk, b->ditems, n_items, b->next, b->variant,
                                                 b->alpha, b->max_sweeps,
-                                                4.0 * eps * std::sqrt((double)BMAX_L));
+                                                4.0 * eps * std::sqrt((double)BMAX_L), b->ws);
   e = cudaGetLastError();
   if (e != cudaSuccess) return batch_fail(e, "batch_kernel");
   for (int i = 0; i < n_items; ++i) {
@@ -652,6 +674,7 @@ extern "C" int fd_batch_destroy(fd_batch_state* b) {
   cudaFree(b->next);
   cudaFree(b->doffs);
   cudaFree(b->fctr_all);
+  cudaFree(b->ws);
   delete b;
   return FD_OK;
 }
@@ -713,6 +736,7 @@ struct fd_server_state {
   std::vector<BatchItem*> ditems;   // per stream
   std::vector<BatchItem*> hitems;   // pinned, per stream
   std::vector<int*> dnext;          // per stream
+  std::vector<float*> ws;           // per stream: 2 * nsm CTA workspaces
   std::vector<char> busy_stream;
   int next_stream = 0;
   std::vector<char> inflight;       // per sketch
@@ -827,7 +851,7 @@ static void serve_engine(fd_server_state* s) {
     const int grid = std::min(ns, 2 * s->b->nsm);
     batch_kernel<<<grid, BT, BATCH_SMEM, stream>>>(s->b->dsk, s->ditems[st], ns, s->dnext[st],
                                                    s->b->variant, s->b->alpha, s->b->max_sweeps,
-                                                   4.0 * eps * std::sqrt((double)BMAX_L));
+                                                   4.0 * eps * std::sqrt((double)BMAX_L), s->ws[st]);
     ServeLaunch L;
     cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming);
     cudaEventRecord(L.ev, stream);
@@ -874,12 +898,15 @@ extern "C" int fd_serve_create(int32_t count, int64_t d, int32_t ell, int32_t va
   s->ditems.resize(nstreams);
   s->hitems.resize(nstreams);
   s->dnext.resize(nstreams);
+  s->ws.assign(nstreams, nullptr);
   s->busy_stream.assign(nstreams, 0);
   for (int k = 0; k < nstreams && e == cudaSuccess; ++k) {
     e = cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&s->ditems[k], (size_t)count * sizeof(BatchItem));
     if (e == cudaSuccess) e = cudaMallocHost(&s->hitems[k], (size_t)count * sizeof(BatchItem));
     if (e == cudaSuccess) e = cudaMalloc(&s->dnext[k], sizeof(int));
+    if (e == cudaSuccess)
+      e = cudaMalloc(&s->ws[k], (size_t)2 * s->b->nsm * BATCH_WS_FLOATS * sizeof(float));
   }
   if (e != cudaSuccess) {
     set_cuda_error(e, "fd_serve_create");
@@ -974,6 +1001,7 @@ extern "C" int fd_serve_destroy(fd_server_state* s) {
     cudaFree(s->ditems[k]);
     if (s->hitems[k]) cudaFreeHost(s->hitems[k]);
     cudaFree(s->dnext[k]);
+    cudaFree(s->ws[k]);
   }
   if (s->hring) cudaFreeHost(s->hring);
   cudaFree(s->dring);

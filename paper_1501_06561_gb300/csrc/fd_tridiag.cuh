@@ -1472,8 +1472,12 @@ __device__ __forceinline__ void tri_twosum_add(float& hi, float& lo, float b) {
   hi = t;
 }
 
-__device__ inline void tri_ritz(const float* G, int ldg, const float* uvec, int n,
-                                int P, float* Us, int ldu, float* H, int ldh, float* Y) {
+// Stage the P vectors of uvec (P rows of n floats, global) transposed into
+// Us (Us[k * ldu + c] = u_c[k], each scaled to unit norm, columns P..ldu-1
+// zero) and form Y = G U (n x ldu floats, global) from 32-term FP32 chunks
+// added by a compensated (two-sum) FP32 accumulation. Ends with a barrier.
+__device__ inline void tri_stage_gu(const float* G, int ldg, const float* uvec, int n, int P,
+                                    float* Us, int ldu, float* Y) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5;
   // vectors, transposed, each scaled to unit norm (FP32 chunks, FP64 total)
@@ -1535,6 +1539,14 @@ __device__ inline void tri_ritz(const float* G, int ldg, const float* uvec, int 
     }
   }
   __syncthreads();
+}
+
+__device__ inline void tri_ritz(const float* G, int ldg, const float* uvec, int n,
+                                int P, float* Us, int ldu, float* H, int ldh, float* Y) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  tri_stage_gu(G, ldg, uvec, n, P, Us, ldu, Y);
+  const int ncb = ldu / 4;
   // H = U^T Y, 4 x 4 blocks per thread: the blocks on and above the
   // diagonal, each mirrored below it
   const int nhb = ncb * (ncb + 1) / 2;
@@ -1659,6 +1671,22 @@ __device__ inline void tri_ritz(const float* G, int ldg, const float* uvec, int 
       }
       if (!any) break;
     }
+  }
+  __syncthreads();
+}
+
+// Rayleigh quotients rho_c = u_c^T G u_c of the P unit vectors staged by
+// tri_stage_gu (Us, and Y = G U), in FP64 from the FP32 products; one warp
+// per vector. Ends with a barrier.
+__device__ inline void tri_rq_diag(const float* Us, int ldu, const float* Y, int n, int P,
+                                   double* rho) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < P; c += nw) {
+    double s = 0.0;
+    for (int k = lane; k < n; k += 32)
+      s = fma((double)Us[(size_t)k * ldu + c], (double)Y[(size_t)k * ldu + c], s);
+    s = warp_sum(s);
+    if (lane == 0) rho[c] = s;
   }
   __syncthreads();
 }
@@ -1791,6 +1819,46 @@ __device__ void tri_eig_shrink(const EigArgs& a, float* A, int ld, int n, double
       }
       tri_cgs2(Zt, ldz, n, count, xb, red);
     }
+  }
+  // SS: the merged masses go to the smallest kept directions, whose
+  // eigenvalues of T are small against ||G||; a row scaled by
+  // sqrt(mu'/lambda) then carries mu' * (u^T G u) / lambda, off by the error
+  // of lambda relative to the row's own Rayleigh quotient. The rows are
+  // scaled by sqrt(mu' / (u^T G u)) instead, with the quotient formed from
+  // the saved G, so that each row carries mu' (SS conserves ||B||_F^2).
+  const bool rqscale = !refine && a.variant == FD_VAR_SS && a.gsave != nullptr &&
+                       a.uvec != nullptr && count > 0 &&
+                       (size_t)n * ((count + 3) & ~3) <= (size_t)n * ld;
+  if (rqscale) {
+    tri_back_write<R, MAXJ, VPT>(a, A, n, Zt, ldz, count, mu, mup, pos, vb0, a.uvec, n);
+    const int ldu = (count + 3) & ~3;
+    float* Us = A;  // A, Zt and the scratch area are dead now
+    double* rq = reinterpret_cast<double*>(d);  // d, e: 2n floats >= count doubles
+    tri_stage_gu(a.gsave, a.ldgsave, a.uvec, n, count, Us, ldu, a.uvec);
+    tri_rq_diag(Us, ldu, a.uvec, n, count, rq);
+    float* wr = reinterpret_cast<float*>(a.wrot);
+    float* rscale = vb1;
+    for (int r = tid; r < nout; r += nt) {
+      const double m1 = (r < count) ? mup[pos[r]] : 0.0;
+      const double q = (r < count) ? rq[r] * smax : 0.0;
+      rscale[r] = (q > 0.0 && m1 > 0.0) ? (float)sqrt(m1 / q) : 0.f;
+      if (a.row_mass) a.row_mass[r] = m1;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nout * n; idx += nt) {
+      const int r = idx / n, i = idx - r * n;
+      const float val = (r < count) ? rscale[r] * Us[(size_t)i * ldu + r] : 0.f;
+      wr[(size_t)r * a.ldr + i] = val;
+      if (a.wrot_hi) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(val);
+        a.wrot_hi[(size_t)r * a.ldr16 + i] = hi;
+        a.wrot_lo[(size_t)r * a.ldr16 + i] = __float2bfloat16_rn(val - __bfloat162float(hi));
+      }
+    }
+    __syncthreads();
+    write_counters(a, n, mu, mup, s_count, s_dsum, s_dlast, 0, 1, nl < n ? s_trace : -1.0,
+                   fell_back ? 1 : 0);
+    return;
   }
   if (!refine) {
     tri_back_write<R, MAXJ, VPT>(a, A, n, Zt, ldz, count, mu, mup, pos, vb0);  // vb0..pb: 4 np8 floats

@@ -29,11 +29,10 @@ def _specs(k, seed):
     return [(int(d), int(e), int(n)) for d, e, n in zip(ds, ells, ns)]
 
 
-_XF_BATCH = pytest.mark.xfail(reason="the batched kernel's eigensolve has no Rayleigh-Ritz refinement: values just above the cut miss the per-value 1e-4 bar (up to 2.6x)", strict=False)
+_XF_BATCH = pytest.mark.xfail(reason="PFD in the batched kernel: a value near the cut of one sketch (d=286, ell=64) at 1.67x the per-value bar; its flushes take the Jacobi solve on the rows present, without the refinement", strict=False)
 
 
-@pytest.mark.parametrize("variant", [pytest.param("fd", marks=_XF_BATCH),
-                                     pytest.param("pfd", marks=_XF_BATCH), "isvd", "ss"])
+@pytest.mark.parametrize("variant", ["fd", pytest.param("pfd", marks=_XF_BATCH), "isvd", "ss"])
 def test_batch_matches_oracle(variant):
     alpha = 0.2 if variant == "pfd" else 1.0
     specs = _specs(24, 7)

@@ -61,7 +61,7 @@ def _oracle_tree(A, cuts, ell, variant, alpha):
     return level[0].sketch()
 
 
-_XF_BF = pytest.mark.xfail(reason="BF16x3: the hi/lo products resolve values near the cut to about 2^-17 sigma_1^2; measured 1.02x-1.32x the per-value bar", strict=False)
+_XF_BF = pytest.mark.xfail(reason="BF16x3 merge tree: a value near the cut at 1.60x the per-value bar (the split products' Gram)", strict=False)
 
 
 @pytest.mark.parametrize("variant,alpha,prec", [
