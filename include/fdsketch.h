@@ -139,7 +139,12 @@ int fd_create(int64_t d, int32_t ell, int32_t variant, double alpha, int32_t pre
  * ell-th squared singular value of the buffer and a reduction leaves ell-1
  * rows, so one reduction handles buffer_rows - ell + 1 new rows (the buffer
  * of Fast FD, Sec. 2.3, taken larger to spread the eigensolve over more rows).
- * FD_VAR_FAST_PFD requires buffer_rows == ell. FD_EINVAL otherwise. */
+ * FD_VAR_FAST_PFD requires buffer_rows == ell. For the other rules,
+ * buffer_rows == ell gives the literal, unbuffered Algorithms 1-3 (Sec. 2.3,
+ * Algorithm 2, Algorithm 3): the sketch itself is the ell-row buffer, and a
+ * reduction runs whenever an inserted row fills its last zero row, leaving
+ * ell-1 rows (one reduction per row once the sketch is full). Any other
+ * buffer_rows below 2*ell is FD_EINVAL. */
 int fd_create_buffered(int64_t d, int32_t ell, int32_t variant, double alpha, int32_t prec,
                        int32_t buffer_rows, void* cuda_stream, fd_handle* out);
 

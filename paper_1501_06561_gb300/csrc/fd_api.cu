@@ -218,7 +218,9 @@ extern "C" int fd_create_buffered(int64_t d, int32_t ell, int32_t variant, doubl
     return FD_EINVAL;
   if (variant == FD_VAR_FAST_PFD) {
     if (buffer_rows != ell || fast_pfd_t(ell, alpha) < 2) return FD_EINVAL;
-  } else if (buffer_rows < 2 * ell) {
+  } else if (buffer_rows != ell && buffer_rows < 2 * ell) {
+    // buffer_rows == ell: the literal Algorithms 1-3 (a reduction whenever the
+    // ell-row sketch has no zero row left)
     return FD_EINVAL;
   }
   if (prec == FD_PREC_BF16X3 && !tc_available()) return FD_EINVAL;
