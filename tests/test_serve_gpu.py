@@ -9,7 +9,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from oracle import cov_err
+from oracle import cov_err, fd_sketch
 from paper_1501_06561_gb300 import fd
 from paper_1501_06561_gb300 import workloads as W
 from helpers import COV_ABS, assert_sigma_parity
@@ -66,3 +66,40 @@ def test_serving_mix_equals_solo():
             na2 = float(np.sum(A.astype(np.float64) ** 2))
             assert_sigma_parity(Bm, Bs, na2, "fp32", what=f"serve sketch {sid}")
             assert abs(cov_err(A, Bm) - cov_err(A, Bs)) <= COV_ABS
+            # and against the FP64 oracle on the same rows
+            Bo, io = fd_sketch(A, ell, "fd", 1.0)
+            assert_sigma_parity(Bm, Bo, io["normA2"], "fp32", what=f"serve sketch {sid} vs oracle")
+            assert abs(cov_err(A, Bm) - cov_err(A, Bo)) <= COV_ABS
+
+
+def test_serving_matches_oracle_at_the_serving_shape():
+    """The serving configuration's sketch shape (d = 512, ell = 32, sparse
+    non-negative rows at 2% density with lognormal row norms, request sizes
+    log-uniform in 1..4,096) on 12 live sketches: every sketch against the
+    FP64 oracle on its own rows, in arrival order."""
+    count, d, ell = 12, 512, 32
+    rng = np.random.default_rng(11)
+    pool = W.sparse_nonneg_rows(40000, d=d, density=0.02, seed=12)
+    per = {i: [] for i in range(count)}
+    pos = 0
+    with fd.FDServer(count, d, ell, budget_bytes=8 * 4096 * d * 4, streams=2) as srv:
+        for _ in range(60):
+            sid = int(rng.integers(0, count))
+            n = int(np.exp(rng.uniform(0, np.log(4096))))
+            if pos + n > pool.shape[0]:
+                pos = 0
+            rows = pool[pos:pos + n]
+            pos += n
+            while srv.submit(sid, rows) is None:
+                time.sleep(1e-4)
+            per[sid].append(rows)
+        srv.drain()
+        srv.poll()
+        for sid in range(count):
+            if not per[sid]:
+                continue
+            A = np.vstack(per[sid])
+            Bm = srv.sketch(sid)
+            Bo, io = fd_sketch(A, ell, "fd", 1.0)
+            assert_sigma_parity(Bm, Bo, io["normA2"], "fp32", what=f"serve {sid} (n={A.shape[0]})")
+            assert abs(cov_err(A, Bm) - cov_err(A, Bo)) <= COV_ABS
