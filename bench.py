@@ -54,9 +54,9 @@ METRIC_SERVE = "serving append latency p99 (ms) and rows/s"
 # buffer rows); profiles/eig_gram_rotate_c1_ell100_full.md.
 EIG_TRAFFIC = {(100, "bf16x3", "fd", 200): 552960}
 # Batched: DRAM bytes per byte of input rows, from a 64-sketch launch of the
-# same generator (1,856,702,104 B for 1,817,569,744 B of rows), scaled by the
+# same generator (1,863,630,000 B for 1,817,569,744 B of rows), scaled by the
 # rows a launch reads; profiles/batch_kernel_c3_64sketch_full.md.
-BATCH_TRAFFIC_PER_INPUT_BYTE = 1856702104 / 1817569744
+BATCH_TRAFFIC_PER_INPUT_BYTE = 1863630000 / 1817569744
 
 
 def parse():
