@@ -52,7 +52,7 @@ METRIC_SERVE = "serving append latency p99 (ms) and rows/s"
 # the configuration it was taken on; None once that kernel changes.
 # Single stream: bytes per eigensolve launch, keyed by (ell, prec, variant,
 # buffer rows); profiles/eig_gram_rotate_c1_ell100_full.md.
-EIG_TRAFFIC = {(100, "bf16x3", "fd", 200): 552960}
+EIG_TRAFFIC = {(100, "bf16x3", "fd", 200): 553728}
 # Batched: DRAM bytes per byte of input rows, from a 64-sketch launch of the
 # same generator (1,863,630,000 B for 1,817,569,744 B of rows), scaled by the
 # rows a launch reads; profiles/batch_kernel_c3_64sketch_full.md.
