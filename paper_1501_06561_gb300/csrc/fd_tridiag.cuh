@@ -12,23 +12,30 @@
 //      last 32 steps run on one warp with the block in registers.
 //   2. Eigenvalues of T from Sturm counts of T - x I (LDL^T pivots): one
 //      count per thread on an even grid brackets every eigenvalue, then
-//      groups of lanes refine each bracket by multisection. Only the ell+1
-//      largest are solved unless SS or a recorded spectrum needs all of
-//      them. Values at or below the bisection's resolution, 2 eps lambda_1,
-//      count as zero.
+//      groups of lanes refine each bracket by multisection to a width of
+//      2 eps |lambda| (relative accuracy). Only the ell+1 largest are solved
+//      unless SS or a recorded spectrum needs all of them. Values at or below
+//      2 eps lambda_1 count as zero.
 //   3. For each retained position r, an eigenvector of T from a twisted
 //      factorisation of T - lambda_r I (forward and backward LDL^T pivots,
 //      twist index at the smallest |gamma|): one thread per vector, O(n).
 //   4. One Cholesky-QR pass (C = Z^T Z = L L^T, Z <- Z L^-T) makes the
 //      vectors orthonormal. If C has a pivot below 1/4 (vectors too close to
-//      dependent, e.g. a multiple eigenvalue), the members of clusters of
-//      close eigenvalues are recomputed by one inverse-iteration solve from a
-//      random start each (pivoted LU) and Cholesky-QR runs again; if a
-//      twisted vector failed or that fails too, every vector is recomputed
-//      that way and orthonormalised by classical Gram-Schmidt twice.
+//      dependent, e.g. a multiple eigenvalue), the members of each tight
+//      group of eigenvalues are recomputed by two rounds of block inverse
+//      iteration from independent starts and made orthonormal within the
+//      group, and Cholesky-QR runs again; if a twisted vector failed or that
+//      fails too, every vector is recomputed by inverse iteration and
+//      orthonormalised by classical Gram-Schmidt twice.
 //   5. u_r = Q z_r = H_0 ... H_{n-3} z_r with each thread holding a strided
 //      slice of one vector in registers; the rotate matrix rows
-//      sqrt(mu'_r / mu_r) u_r go straight to their destination.
+//      sqrt(mu'_r / mu_r) u_r go straight to their destination, or (step 6)
+//      the raw vectors go to a global scratch.
+//   6. Rayleigh-Ritz with the saved original G for positions 0..ell (FD,
+//      PFD, iSVD): H = U^T G U with compensated sums, Jacobi rotations on H,
+//      the Ritz values in place of T's eigenvalues for the shrink, and the
+//      rotate matrix from the rotated vectors. SS instead scales its rows by
+//      the Rayleigh quotients of its vectors.
 //
 // Memory: A (n x ld floats, ld >= n) holds G on entry; afterwards its front
 // holds the packed reflectors (n(n-1)/2 floats) and, from tri_zoff(n), the
