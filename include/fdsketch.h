@@ -315,8 +315,16 @@ typedef struct {
 
 int fd_batch_create(int32_t count, const int64_t* d, const int32_t* ell, int32_t variant,
                     double alpha, int32_t prec, void* cuda_stream, fd_batch* out);
-/* Append row blocks to sketches; asynchronous on the batch's stream. */
+/* Append row blocks to sketches; asynchronous on the batch's stream. The
+ * append is a CUDA graph (the queue reset and the persistent launch, captured
+ * on the first call and relaunched for every call); only the item table and
+ * its length are copied in before each launch, from pinned host memory. The
+ * call waits for the previous call's item copy (not its kernel) before it
+ * refills that memory. If the graph cannot be built, appends launch directly. */
 int fd_batch_append(fd_batch b, const fd_work_t* items, int32_t n_items);
+/* 1 if appends run as the CUDA graph, 0 if they launch directly (FD_EINVAL for
+ * a null batch); *launches (optional) receives the graph launches so far. */
+int fd_batch_uses_graph(fd_batch b, int64_t* launches);
 /* Sketch `id` as ell_id x d_id rows (same flush rule as fd_sketch). */
 int fd_batch_sketch(fd_batch b, int32_t id, void* out, int32_t dtype, int32_t out_on_device);
 /* Every sketch at once, into one device buffer of FP32: sketch id is written

@@ -294,7 +294,7 @@ __device__ void batch_reduce(const BatchSketch& S, int nrows, float* out, long l
 __global__ void __launch_bounds__(BT, 2)
     batch_kernel(BatchSketch* __restrict__ sk, const BatchItem* __restrict__ items, int nitems,
                  int* __restrict__ next, int variant, double alpha, int max_sweeps,
-                 double tol, float* ws_all) {
+                 double tol, float* ws_all, const int* __restrict__ nitems_dev) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   __shared__ double s_rn[BMAX_L];
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(BT, 2)
     if (tid == 0) s_item = atomicAdd(next, 1);
     __syncthreads();
     const int it = s_item;
-    if (it >= nitems) break;
+    if (it >= (nitems_dev ? *nitems_dev : nitems)) break;
     const BatchItem item = items[it];
     BatchSketch S = sk[item.id];
     int m = S.m;
@@ -410,6 +410,21 @@ struct fd_batch_state {
   long long* doffs = nullptr;     // device copy of the sketch_all offsets
   DevCounters* fctr_all = nullptr;
   float* ws = nullptr;            // 2 * nsm CTA workspaces (BATCH_WS_FLOATS each)
+  // The CUDA graph of an append: the queue-counter reset and the persistent
+  // launch (2 x SMs CTAs; those beyond the work exit at once), with the item
+  // table and its length read from fixed device buffers. Captured once, on
+  // the first append, and relaunched for every append; the items are copied
+  // in from pinned host memory before each launch.
+  cudaStream_t cap_st = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  BatchItem* gitems = nullptr;    // device, count entries
+  BatchItem* hitems = nullptr;    // pinned, count entries
+  int* dcount = nullptr;          // device item count
+  int* hcount = nullptr;          // pinned
+  cudaEvent_t ev_copy = nullptr;  // the last append's copies have been read
+  bool copy_pending = false;
+  bool graph_off = false;
+  long long graph_launches = 0;
 };
 
 static int batch_fail(cudaError_t e, const char* w) {
@@ -496,6 +511,49 @@ extern "C" int fd_batch_create(int32_t count, const int64_t* d, const int32_t* e
   return FD_OK;
 }
 
+// Capture the append graph (once per batch). False if any step fails; the
+// caller then launches directly.
+static bool batch_graph_build(fd_batch_state* b) {
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&b->gitems, (size_t)b->count * sizeof(BatchItem));
+  if (e == cudaSuccess) e = cudaMalloc(&b->dcount, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->hitems, (size_t)b->count * sizeof(BatchItem));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->hcount, sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_copy, cudaEventDisableTiming);
+  if (e != cudaSuccess) return false;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return false;
+  const double eps = 1.1920928955078125e-07;
+  cudaError_t e1 = cudaMemsetAsync(b->next, 0, sizeof(int), b->cap_st);
+  if (e1 == cudaSuccess) {
+    batch_kernel<<<2 * b->nsm, BT, BATCH_SMEM, b->cap_st>>>(
+        b->dsk, b->gitems, 0, b->next, b->variant, b->alpha, b->max_sweeps,
+        4.0 * eps * std::sqrt((double)BMAX_L), b->ws, b->dcount);
+    e1 = cudaGetLastError();
+  }
+  e = cudaStreamEndCapture(b->cap_st, &g);
+  if (e1 != cudaSuccess || e != cudaSuccess || g == nullptr) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return false;
+  }
+  e = cudaGraphInstantiate(&b->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b->gexec = nullptr;
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+extern "C" int fd_batch_uses_graph(fd_batch_state* b, int64_t* launches) {
+  if (!b) return FD_EINVAL;
+  if (launches) *launches = b->graph_launches;
+  return (b->gexec != nullptr && !b->graph_off) ? 1 : 0;
+}
+
 extern "C" int fd_batch_append(fd_batch_state* b, const fd_work_t* items, int32_t n_items) {
   if (!b || (n_items > 0 && !items) || n_items < 0) return FD_EINVAL;
   if (n_items == 0) return FD_OK;
@@ -519,24 +577,44 @@ extern "C" int fd_batch_append(fd_batch_state* b, const fd_work_t* items, int32_
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
   std::vector<BatchItem> sorted(n_items);
   for (int i = 0; i < n_items; ++i) sorted[i] = hi[order[i]];
-  if (n_items > b->items_cap) {
-    cudaFree(b->ditems);
-    b->ditems = nullptr;
-    cudaError_t e = cudaMalloc(&b->ditems, (size_t)n_items * sizeof(BatchItem));
-    if (e != cudaSuccess) return batch_fail(e, "batch items");
-    b->items_cap = n_items;
+  if (!b->graph_off && b->gexec == nullptr && !batch_graph_build(b)) b->graph_off = true;
+  if (!b->graph_off) {
+    // the previous append's item copy must have been read before the pinned
+    // table is refilled
+    cudaError_t e = b->copy_pending ? cudaEventSynchronize(b->ev_copy) : cudaSuccess;
+    if (e != cudaSuccess) return batch_fail(e, "batch item copy wait");
+    std::memcpy(b->hitems, sorted.data(), (size_t)n_items * sizeof(BatchItem));
+    *b->hcount = n_items;
+    e = cudaMemcpyAsync(b->gitems, b->hitems, (size_t)n_items * sizeof(BatchItem),
+                        cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->dcount, b->hcount, sizeof(int), cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_copy, b->st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->gexec, b->st);
+    if (e != cudaSuccess) return batch_fail(e, "batch graph launch");
+    b->copy_pending = true;
+    ++b->graph_launches;
+  } else {
+    if (n_items > b->items_cap) {
+      cudaFree(b->ditems);
+      b->ditems = nullptr;
+      cudaError_t e = cudaMalloc(&b->ditems, (size_t)n_items * sizeof(BatchItem));
+      if (e != cudaSuccess) return batch_fail(e, "batch items");
+      b->items_cap = n_items;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->ditems, sorted.data(), (size_t)n_items * sizeof(BatchItem),
+                                    cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->next, 0, sizeof(int), b->st);
+    if (e != cudaSuccess) return batch_fail(e, "batch items copy");
+    const int grid = std::min(n_items, 2 * b->nsm);
+    const double eps = 1.1920928955078125e-07;
+    batch_kernel<<<grid, BT, BATCH_SMEM, b->st>>>(b->dsk, b->ditems, n_items, b->next, b->variant,
+                                                  b->alpha, b->max_sweeps,
+                                                  4.0 * eps * std::sqrt((double)BMAX_L), b->ws,
+                                                  nullptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return batch_fail(e, "batch_kernel");
   }
-  cudaError_t e = cudaMemcpyAsync(b->ditems, sorted.data(), (size_t)n_items * sizeof(BatchItem),
-                                  cudaMemcpyHostToDevice, b->st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->next, 0, sizeof(int), b->st);
-  if (e != cudaSuccess) return batch_fail(e, "batch items copy");
-  const int grid = std::min(n_items, 2 * b->nsm);
-  const double eps = 1.1920928955078125e-07;
-  batch_kernel<<<grid, BT, BATCH_SMEM, b->st>>>(b->dsk, b->ditems, n_items, b->next, b->variant,
-                                                b->alpha, b->max_sweeps,
-                                                4.0 * eps * std::sqrt((double)BMAX_L), b->ws);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return batch_fail(e, "batch_kernel");
   for (int i = 0; i < n_items; ++i) {
     const int id = items[i].id;
     const int L = 2 * b->ell[id];
@@ -675,6 +753,13 @@ extern "C" int fd_batch_destroy(fd_batch_state* b) {
   cudaFree(b->doffs);
   cudaFree(b->fctr_all);
   cudaFree(b->ws);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->cap_st) cudaStreamDestroy(b->cap_st);
+  cudaFree(b->gitems);
+  cudaFree(b->dcount);
+  if (b->hitems) cudaFreeHost(b->hitems);
+  if (b->hcount) cudaFreeHost(b->hcount);
+  if (b->ev_copy) cudaEventDestroy(b->ev_copy);
   delete b;
   return FD_OK;
 }
@@ -851,7 +936,8 @@ static void serve_engine(fd_server_state* s) {
     const int grid = std::min(ns, 2 * s->b->nsm);
     batch_kernel<<<grid, BT, BATCH_SMEM, stream>>>(s->b->dsk, s->ditems[st], ns, s->dnext[st],
                                                    s->b->variant, s->b->alpha, s->b->max_sweeps,
-                                                   4.0 * eps * std::sqrt((double)BMAX_L), s->ws[st]);
+                                                   4.0 * eps * std::sqrt((double)BMAX_L), s->ws[st],
+                                                   nullptr);
     ServeLaunch L;
     cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming);
     cudaEventRecord(L.ev, stream);

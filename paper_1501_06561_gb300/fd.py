@@ -86,6 +86,7 @@ def load():
         "fd_batch_stats": [vp, i32, ctypes.POINTER(Stats)],
         "fd_batch_sketch_all": [vp, vp, ctypes.POINTER(i64)],
         "fd_batch_reset": [vp],
+        "fd_batch_uses_graph": [vp, ctypes.POINTER(i64)],
         "fd_cov_err_noalloc": [vp, i64, i64, i64, i32, vp, i64, i32, vp, ctypes.POINTER(dbl)],
         "fd_serve_create": [i32, i64, i32, i32, dbl, i64, i32, ctypes.POINTER(vp)],
         "fd_serve_submit": [vp, i32, vp, i64, ctypes.POINTER(i64)],
@@ -420,6 +421,14 @@ class FDBatch:
 
     def reset(self):
         _check(load().fd_batch_reset(self._h), "fd_batch_reset")
+
+    def uses_graph(self):
+        """(whether appends run as the captured CUDA graph, graph launches so far)."""
+        n = ctypes.c_int64(0)
+        rc = load().fd_batch_uses_graph(self._h, ctypes.byref(n))
+        if rc < 0:
+            _check(rc, "fd_batch_uses_graph")
+        return bool(rc), int(n.value)
 
     def close(self):
         if getattr(self, "_h", None):

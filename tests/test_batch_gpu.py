@@ -109,3 +109,24 @@ def test_batch_rejects_bad_items():
             b.append({5: x})
     with pytest.raises(fd.FDError):
         fd.FDBatch([64], [65])    # 2*ell > 128
+
+
+def test_batch_appends_run_as_a_cuda_graph():
+    """Appends are relaunches of one captured CUDA graph. Appending each
+    stream in three blocks gives exactly the sketch of one append of the
+    whole stream (same rows, same order, same reductions)."""
+    specs = _specs(6, 23)
+    data = [W.random_noisy(n, d, m=4, seed=80 + i, dtype=np.float32)
+            for i, (d, e, n) in enumerate(specs)]
+    dev = [torch.from_numpy(a).cuda() for a in data]
+    with fd.FDBatch([s[0] for s in specs], [s[1] for s in specs]) as b1, \
+         fd.FDBatch([s[0] for s in specs], [s[1] for s in specs]) as b3:
+        b1.append({i: a for i, a in enumerate(dev)})
+        for part in range(3):
+            b3.append({i: a[part * a.shape[0] // 3:(part + 1) * a.shape[0] // 3]
+                       for i, a in enumerate(dev)})
+        on1, n1 = b1.uses_graph()
+        on3, n3 = b3.uses_graph()
+        assert on1 and on3 and (n1, n3) == (1, 3)
+        for i in range(len(specs)):
+            np.testing.assert_array_equal(b1.sketch(i), b3.sketch(i))
