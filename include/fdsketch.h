@@ -61,22 +61,22 @@ enum { FD_VAR_FD = 0, FD_VAR_PFD = 1, FD_VAR_SS = 2, FD_VAR_ISVD = 3, FD_VAR_FAS
 
 /* Arithmetic of the reduction.
  * FD_PREC_FP32:   FP32 buffer, FP32 CUDA-core Gram and rotate, FP32
- *                 eigensolve (tridiagonal: Householder reduction, bisection,
- *                 twisted-factorisation vectors, Cholesky-QR; one-sided
- *                 Jacobi for the flush of a partial buffer); shrink and
- *                 bookkeeping in FP64.
+ *                 eigensolve (tridiagonal: Householder reduction, bisection
+ *                 to relative accuracy, twisted-factorisation vectors,
+ *                 Cholesky-QR, then a Rayleigh-Ritz step with the original
+ *                 Gram for FD, PFD and iSVD); a flush of a partial buffer is
+ *                 solved at the full buffer size with the missing rows zero;
+ *                 shrink and bookkeeping in FP64.
  * FD_PREC_BF16X3: buffer held as bfloat16 hi/lo pairs; Gram and rotate on the
  *                 tcgen05 tensor cores as split products hi*hi + hi*lo + lo*hi
- *                 accumulated in FP32 (TMEM); the same FP32 eigensolve; FP64
- *                 shrink. Its values carry about 2^-16 of rounding per
- *                 reduction and a small low bias, which add up along
- *                 directions that stay for thousands of reductions. On a
- *                 stream of 200,000 x 2,000 rows at ell = 100 (1,979
- *                 reductions) its cov-err ends 4.3e-5 above the FP64
- *                 run's and above that run's Delta / ||A||_F^2, the bound
- *                 of Lemma 1 (Sec. 3.1); FD_PREC_FP32 ends 1.5e-6 from the
- *                 FP64 run. Use
- *                 FD_PREC_FP32 where that bound must hold on long streams.
+ *                 (each K step in a fresh TMEM accumulator, the steps added in
+ *                 FP32 registers, the mean shortfall of the MMA's rounding
+ *                 toward zero added back); the Gram's diagonal from the FP64
+ *                 squared norms of the stored rows; the same FP32 eigensolve;
+ *                 FP64 shrink. Its values carry about 2^-16 of rounding per
+ *                 reduction. On a stream of 200,000 x 2,000 rows at ell = 100
+ *                 (1,979 reductions) its cov-err ends within 1e-6 of the FP64
+ *                 run's and its singular values within 1e-4 of them.
  * FD_PREC_FP64:   FP64 buffer, FP64 Gram, rotate and Jacobi (slow; for
  *                 checking against FP64 references). */
 enum { FD_PREC_FP32 = 0, FD_PREC_BF16X3 = 1, FD_PREC_FP64 = 2 };

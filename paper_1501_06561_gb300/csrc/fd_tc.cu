@@ -4,7 +4,10 @@
 // Split precision. Every FP32 value x of the buffer is held as two bfloat16
 // numbers hi = bf16(x), lo = bf16(x - hi), so x = hi + lo to about 2^-17.
 // A product x*y is taken as hi_x*hi_y + hi_x*lo_y + lo_x*hi_y (the lo*lo term,
-// about 2^-16 of the product, is dropped) and accumulated in FP32.
+// about 2^-16 of the product, is dropped) and accumulated in FP32: each K step
+// of 16 in a fresh TMEM accumulator, the steps added in registers. The Gram's
+// diagonal, where lo*lo is a sum of squares, is replaced by the eigensolve
+// with FP64 squared norms of the stored rows.
 //
 // Buffer layout in HBM (one sketch of width d, buffer of L rows, L = 2*ell by default):
 //   rm_hi, rm_lo2: row-major  L x ldb  (ldb = d rounded up to 64), lo2 = 2*lo
