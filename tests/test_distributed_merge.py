@@ -169,3 +169,27 @@ def test_gpu_fold_of_parts_matches_the_oracle_replay():
     assert abs(stg["norm_a2"] - io["normA2"]) <= 1e-12 * io["normA2"]
     assert_sigma_parity(Bg, Bo, io["normA2"], "fp64", what="distributed fold")
     assert abs(cov_err(A, Bg) - cov_err(A, Bo)) <= COV_ABS
+
+
+def test_fold_with_empty_parts_equals_replay():
+    """More ranks than rows leaves some parts empty: their packed sketches
+    carry no rows and zero counters, and the fold gives the oracle's sketch
+    of the rows that exist (the merge of an empty sketch is the identity)."""
+    A = W.random_noisy(5, DIM, m=3, seed=33, dtype=np.float64)
+    world = 8
+    gathered = []
+    for r in range(world):
+        r0, r1 = D.shard_bounds(A.shape[0], world, r)
+        o = FDOracle(DIM, ELL, "fd")
+        o.append(A[r0:r1])
+        B, info = o.sketch()
+        st = dict(d=DIM, ell=ELL, n_seen=info["n_seen"], reductions=info["reductions"],
+                  norm_a2=info["normA2"], sketch_sum_delta=info["sum_delta"],
+                  sketch_removed=info["removed"])
+        gathered.append(D.unpack(D.pack(B, st), ELL, DIM))
+    assert sum(rows.shape[0] == 0 for rows, _ in gathered) == world - A.shape[0]
+    root, _ = D.fold(lambda: OracleSketch(DIM, ELL), gathered)
+    Bm, info = root.o.sketch()
+    # fewer than ell rows in all: exact recovery, no reduction, Delta = 0
+    np.testing.assert_allclose(Bm.T @ Bm, A.T @ A, rtol=0, atol=1e-10 * float(np.sum(A * A)))
+    assert info["sum_delta"] == 0.0 and info["n_seen"] == A.shape[0]
