@@ -824,8 +824,10 @@ def main():
         "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"bf16x3": "bf16x3 (fp32 accumulate), fp32 eig, f64 shrink",
-                  "fp32": "f32, f64 shrink", "fp64": "f64"}[w["prec"]],
+        "dtype": {"bf16x3": "bf16x3 (fp32 accumulate), fp32 eig refined with the original Gram, "
+                            "f64 shrink",
+                  "fp32": "f32, fp32 eig refined with the original Gram, f64 shrink",
+                  "fp64": "f64"}[w["prec"]],
         "data": "synthetic",
         "config": {"workload": w["name"], "ell": w["ell"], "variant": w["variant"],
                    "alpha": w["alpha"], "prec": w["prec"], "rows_per_step": w["n"],
