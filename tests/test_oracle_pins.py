@@ -514,6 +514,25 @@ def test_fast_alpha_fd_fixed_cadence_equals_literal(ell, alpha):
     np.testing.assert_allclose(Bb.T @ Bb, Bl.T @ Bl, rtol=0, atol=1e-9 * ib["normA2"])
 
 
+@pytest.mark.parametrize("variant,alpha", [("fd", 1.0), ("pfd", 0.25), ("isvd", 1.0), ("ss", 1.0)])
+def test_literal_reduces_at_every_row_once_full(variant, alpha):
+    """Algorithm 1 as printed (the literal mode): for generic data a reduction
+    of the full ell-row sketch frees exactly one row (FD and alpha-FD zero
+    sigma_ell only, iSVD drops it, SS merges one pair), so once the sketch is
+    full every row triggers a reduction: n - ell + 1 of them, with ell - 1
+    nonzero rows after each. A GPU sketch with an ell-row buffer keeping
+    ell - 1 rows follows the same cadence."""
+    ell, n = 8, 120
+    A = W.random_noisy(n, 30, m=5, seed=91, dtype=np.float64)
+    o = FDOracle(30, ell, variant, alpha, mode="literal")
+    for i in range(n):
+        o.append(A[i:i + 1])
+        nz = int(np.count_nonzero(np.any(o.buf != 0.0, axis=1)))
+        if i + 1 >= ell:
+            assert nz == ell - 1, (i, nz)
+    assert o.reductions == n - ell + 1
+
+
 # --------------------------------------------------------------------------
 # The oracle's own SVD (one-sided Jacobi) against the textbook SVD and a
 # closed form; whole streams through either SVD route agree
